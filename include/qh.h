@@ -1,0 +1,174 @@
+/*
+ * qh.h -- C ABI of the GB300 segmented-QuickHull library (libqh.so).
+ *
+ * Method: Zhang, Mei, Xu, Zhao, "A Novel Implementation of QuickHull Algorithm
+ * on the GPU".  The library computes the convex hull of planar FP32 point sets
+ * (Sec. 1: "the convex polygon that encloses all the points") with the
+ * segmented, generation-synchronous QuickHull of Sec. 3-4: extreme points and an
+ * initial split (Sec. 4.2-4.3), then rounds of farthest point per segment
+ * (Sec. 4.4.1), segment update (Sec. 4.4.2, 4.4.4) and discard of interior
+ * points (Sec. 4.4.3) until no segment holds points.
+ *
+ * Output convention (every entry point): indices of the strictly convex hull
+ * vertices, counter-clockwise, starting at the lexicographically smallest
+ * (x, then y) point.  Points on a hull edge are not vertices.  Points with
+ * identical coordinates (compared by value, -0 == +0) are represented by their
+ * lowest index.  Every geometric decision is exact: FP32 (or FP64) arithmetic
+ * with a certified error bound, and an exact fallback where the bound cannot
+ * decide.
+ *
+ * Memory: every pointer argument named "device" must be device memory of the
+ * current CUDA device; "host" pointers are host memory.  Points are interleaved
+ * x, y float pairs (8-byte aligned).  The caller owns inputs and outputs; a
+ * plan owns all scratch memory.  Calls are stream-ordered and asynchronous
+ * unless stated otherwise: the results are valid once the stream has reached
+ * the call.  Host-detected errors return immediately; errors detected on the
+ * device are written into the output counts as the negated status code.
+ * A plan must not be used by two streams at the same time.
+ */
+#ifndef QH_H
+#define QH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Compatible with cudaStream_t. */
+typedef struct CUstream_st *qh_stream_t;
+
+typedef enum {
+    QH_OK = 0,
+    QH_ERR_INVALID_ARG = 1, /* bad pointer, size or flag */
+    QH_ERR_NONFINITE = 2,   /* an input coordinate is NaN or infinite */
+    QH_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    QH_ERR_OOM = 4,         /* device memory allocation failed */
+    QH_ERR_CAPACITY = 5,    /* input larger than the plan, or a device table overflowed */
+    QH_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (status word set) */
+    QH_ERR_INTERNAL = 7,    /* inconsistent device state */
+    QH_ERR_UNSUPPORTED = 8  /* not possible in this context (e.g. growing a plan during capture) */
+} qh_status;
+
+/* Plan flags. */
+#define QH_MODE_QUAD 0x0u   /* initial quadrilateral of the 4 extreme points (paper's Mode 1, Sec. 4.2) */
+#define QH_MODE_CHORD 0x1u  /* initial chord leftmost->rightmost only (paper's Mode 2, Sec. 4.3) */
+#define QH_PREC_F32 0x0u    /* FP32 predicates with certified bound + exact fallback */
+#define QH_PREC_F64 0x2u    /* plain FP64 predicates with bound + the same exact fallback */
+
+#define QH_MAX_GEN 64
+
+typedef struct qh_plan_s *qh_plan;
+
+typedef struct {
+    int32_t device_status;      /* 0, or the qh_status of the first device-side failure */
+    int32_t global_rounds;      /* grid-wide rounds after the initial split */
+    int32_t generations;        /* generations run (initial split = generation 0) */
+    int32_t small_problems;     /* segments and sets finished by one thread block each */
+    int32_t nodes;              /* segments created by grid-wide rounds */
+    int32_t big_sets;           /* point sets that took the grid-wide path */
+    int64_t live[QH_MAX_GEN];   /* points held by segments after each generation (all sets) */
+    int64_t exact_orient;       /* orientation tests decided by the exact fallback */
+    int64_t exact_compare;      /* farthest-point comparisons decided by the exact fallback */
+    float phase_ms[5];          /* with timing on: grid rounds, finisher, emit, copy, total */
+} qh_stats;
+
+/*
+ * qh_plan_create -- allocate a plan for up to max_points points in up to
+ * max_sets sets.  flags: QH_MODE_* | QH_PREC_*.  The plan holds roughly
+ * 64 bytes of device scratch per point.  Errors: QH_ERR_INVALID_ARG (sizes < 1),
+ * QH_ERR_OOM, QH_ERR_CUDA.
+ */
+qh_status qh_plan_create(int64_t max_points, int32_t max_sets, uint32_t flags, qh_plan *out);
+
+/* Release a plan (synchronizes the device first).  NULL is accepted. */
+qh_status qh_plan_destroy(qh_plan plan);
+
+/* Change mode/precision flags of an existing plan (no reallocation). */
+qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags);
+
+/*
+ * Tuning knobs.  cutover: segments with at most this many points are finished
+ * by one thread block in shared memory (2048 <= cutover <= 4096).  timing: 1
+ * records CUDA events between the kernels so qh_plan_get_stats can report
+ * per-phase times.  grid_ctas_per_sm: 0 = occupancy maximum.
+ */
+qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int32_t grid_ctas_per_sm);
+
+/*
+ * qh_hull2d_p -- hull of one point set (Sec. 1).
+ *   points:    device, float[2*n] interleaved x,y; read only.
+ *   n:         number of points, 0 <= n <= the plan's max_points.
+ *   out_idx:   device int32[n] (any capacity >= n); receives the hull vertex
+ *              indices (CCW from the lexicographic minimum).
+ *   out_count: device int32[1]; receives the vertex count, or -status on a
+ *              device-detected error (QH_ERR_NONFINITE, QH_ERR_TIMEOUT, ...).
+ *   stream:    CUDA stream (NULL = legacy default stream).
+ * Returns QH_OK once the work is enqueued.
+ */
+qh_status qh_hull2d_p(qh_plan plan, const float *points, int64_t n, int32_t *out_idx,
+                      int32_t *out_count, qh_stream_t stream);
+
+/*
+ * qh_hull2d -- as qh_hull2d_p with a per-device default plan (QUAD, FP32) that
+ * grows on demand.  Growing synchronizes the device and is refused
+ * (QH_ERR_UNSUPPORTED) while the stream is being captured.
+ */
+qh_status qh_hull2d(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                    qh_stream_t stream);
+
+/*
+ * qh_hull2d_batched -- hulls of num_sets independent point sets in one call.
+ *   points:     device, float[2*N] interleaved x,y of all sets.
+ *   offsets:    device int64[num_sets+1], non-decreasing, offsets[0] >= 0,
+ *               offsets[num_sets] <= the plan's max_points; set s is
+ *               points[offsets[s] .. offsets[s+1]).
+ *   out_idx:    device int32[offsets[num_sets]]; set s's hull (indices local
+ *               to the set) is written at out_idx + offsets[s].
+ *   out_counts: device int32[num_sets]; vertex count of each set, or -status.
+ * The result equals num_sets separate qh_hull2d_p calls.  No host
+ * synchronization; the call can be captured in a CUDA graph.
+ */
+qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *offsets, int32_t num_sets,
+                            int32_t *out_idx, int32_t *out_counts, qh_stream_t stream);
+
+/*
+ * qh_hull2d_host -- end-to-end form of qh_hull2d_p with HOST buffers: copies
+ * host_points (float[2*n]) to the device, computes, copies the hull to
+ * host_out_idx (int32[n]) and the count to *host_out_count, and synchronizes
+ * the stream before returning.  Pinned host memory gives the fastest copies.
+ */
+qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
+                         int32_t *host_out_count, qh_stream_t stream);
+
+/* Statistics of the plan's last call; synchronizes the plan's last stream. */
+qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out);
+
+/* Static description of a status code. */
+const char *qh_status_string(qh_status s);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t qh_version(void);
+
+/*
+ * Predicate check hooks (used by the test suite; the hull itself never calls
+ * them).  qh_check_orient_host evaluates, on the CPU, the same filtered
+ * orientation code the kernels run: sign[k] is the decided sign of
+ * orient(a_k, b_k, c_k) for the triples tri[6k .. 6k+6) = ax ay bx by cx cy,
+ * and certified[k] is 1 when the filter (prec: 0 = FP32, 1 = FP64) decided it
+ * without the exact fallback.  qh_check_orient_device runs the same on the
+ * GPU with device arrays.  qh_check_dist_* return sign(dist(P) - dist(Q)) for
+ * quads[8k .. 8k+8) = ux uy vx vy px py qx qy, where dist(X) is the distance
+ * of X to the right of the chord u->v.
+ */
+qh_status qh_check_orient_host(const float *tri, int64_t n, int32_t prec, int32_t *sign, int32_t *certified);
+qh_status qh_check_orient_device(const float *tri, int64_t n, int32_t prec, int32_t *sign, int32_t *certified,
+                                 qh_stream_t stream);
+qh_status qh_check_dist_host(const float *quads, int64_t n, int32_t *sign);
+qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QH_H */

@@ -1,0 +1,251 @@
+"""Python binding of libqh.so, the GB300 segmented-QuickHull library.
+
+Argument marshalling only: every step of the hull runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The library must have
+been built (``__graft_entry__.build()`` or ``python -m paper_1501_04706_gb300.build``);
+loading fails loudly otherwise -- there is no CPU fallback.
+
+Method: Zhang, Mei, Xu, Zhao, "A Novel Implementation of QuickHull Algorithm on
+the GPU" (segmented QuickHull, Sec. 3-4).  Output: CCW hull vertex indices from
+the lexicographically smallest point, collinear boundary points excluded,
+duplicates represented by their lowest index.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+__all__ = [
+    "QhError", "Plan", "load", "hull2d", "hull2d_batched", "hull2d_host", "check_orient_host",
+    "check_orient_device", "check_dist_host", "check_dist_device", "MODE_QUAD", "MODE_CHORD",
+    "PREC_F32", "PREC_F64", "STATUS",
+]
+
+MODE_QUAD, MODE_CHORD = 0x0, 0x1
+PREC_F32, PREC_F64 = 0x0, 0x2
+MAX_GEN = 64
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "non-finite input coordinate", 3: "CUDA runtime error",
+          4: "out of device memory", 5: "capacity exceeded", 6: "device-side wait timed out",
+          7: "internal error", 8: "unsupported in this context"}
+
+
+class QhError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("device_status", ctypes.c_int32), ("global_rounds", ctypes.c_int32),
+                ("generations", ctypes.c_int32), ("small_problems", ctypes.c_int32),
+                ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32),
+                ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
+                ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libqh.so (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libqh.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.qh_plan_create.argtypes = [i64, i32, u32, ctypes.POINTER(vp)]
+    lib.qh_plan_destroy.argtypes = [vp]
+    lib.qh_plan_set_flags.argtypes = [vp, u32]
+    lib.qh_plan_set_tuning.argtypes = [vp, i32, i32, i32]
+    lib.qh_hull2d_p.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.qh_hull2d.argtypes = [vp, i64, vp, vp, vp]
+    lib.qh_hull2d_batched.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    lib.qh_hull2d_host.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.qh_plan_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.qh_status_string.argtypes = [ctypes.c_int]
+    lib.qh_status_string.restype = ctypes.c_char_p
+    lib.qh_version.restype = i32
+    lib.qh_check_orient_host.argtypes = [vp, i64, i32, vp, vp]
+    lib.qh_check_orient_device.argtypes = [vp, i64, i32, vp, vp, vp]
+    lib.qh_check_dist_host.argtypes = [vp, i64, vp]
+    lib.qh_check_dist_device.argtypes = [vp, i64, vp, vp]
+    for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_hull2d_p",
+              "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_plan_get_stats", "qh_check_orient_host",
+              "qh_check_orient_device", "qh_check_dist_host", "qh_check_dist_device"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise QhError(st, where)
+
+
+def _stream(device=None) -> int:
+    import torch
+
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Plan:
+    """Device scratch for hulls of up to ``max_points`` points in up to ``max_sets`` sets."""
+
+    def __init__(self, max_points: int, max_sets: int = 1, mode: int = MODE_QUAD, prec: int = PREC_F32):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.qh_plan_create(int(max_points), int(max_sets), mode | prec, ctypes.byref(h)), "qh_plan_create")
+        self.handle = h
+        self.max_points = int(max_points)
+        self.max_sets = int(max_sets)
+
+    def close(self) -> None:
+        if self.handle:
+            load().qh_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_flags(self, mode: int = MODE_QUAD, prec: int = PREC_F32) -> None:
+        _check(load().qh_plan_set_flags(self.handle, mode | prec), "qh_plan_set_flags")
+
+    def set_tuning(self, cutover: int = 4096, timing: bool = False, ctas_per_sm: int = 0) -> None:
+        _check(load().qh_plan_set_tuning(self.handle, int(cutover), int(bool(timing)), int(ctas_per_sm)),
+               "qh_plan_set_tuning")
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(load().qh_plan_get_stats(self.handle, ctypes.byref(s)), "qh_plan_get_stats")
+        g = s.generations
+        return {"device_status": s.device_status, "global_rounds": s.global_rounds, "generations": g,
+                "small_problems": s.small_problems, "nodes": s.nodes, "big_sets": s.big_sets,
+                "live": [int(v) for v in s.live[: min(g, MAX_GEN)]], "exact_orient": int(s.exact_orient),
+                "exact_compare": int(s.exact_compare), "phase_ms": [float(v) for v in s.phase_ms]}
+
+
+def _points_tensor(points):
+    import torch
+
+    if not isinstance(points, torch.Tensor) or not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor")
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 2:
+        raise ValueError("points must be float32 of shape [n, 2]")
+    return points.contiguous()
+
+
+def hull2d(points, plan: Plan | None = None, out=None, count=None, sync: bool = True):
+    """Hull of one point set (CUDA float32 tensor [n, 2]).
+
+    Returns the int32 index tensor (synchronizes to read the count) or, with
+    ``sync=False``, the (out, count) device tensors without synchronizing.
+    """
+    import torch
+
+    lib = load()
+    pts = _points_tensor(points)
+    n = pts.shape[0]
+    dev = pts.device
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int32, device=dev)
+    s = _stream(dev)
+    if plan is None:
+        st = lib.qh_hull2d(pts.data_ptr(), n, out.data_ptr(), count.data_ptr(), s)
+    else:
+        st = lib.qh_hull2d_p(plan.handle, pts.data_ptr(), n, out.data_ptr(), count.data_ptr(), s)
+    _check(st, "qh_hull2d")
+    if not sync:
+        return out, count
+    c = int(count.item())
+    if c < 0:
+        raise QhError(-c, "qh_hull2d (device)")
+    return out[:c]
+
+
+def hull2d_batched(points, offsets, plan: Plan, out=None, counts=None):
+    """Hulls of a CSR batch; returns (out int32[N], counts int32[num_sets]) without synchronizing.
+
+    Set s's hull (indices local to the set) is out[offsets[s] : offsets[s] + counts[s]].
+    """
+    import torch
+
+    lib = load()
+    pts = _points_tensor(points)
+    off = offsets.to(device=pts.device, dtype=torch.int64).contiguous()
+    num_sets = off.shape[0] - 1
+    if out is None:
+        out = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=pts.device)
+    if counts is None:
+        counts = torch.empty(max(num_sets, 1), dtype=torch.int32, device=pts.device)
+    _check(lib.qh_hull2d_batched(plan.handle, pts.data_ptr(), off.data_ptr(), num_sets, out.data_ptr(),
+                                 counts.data_ptr(), _stream(pts.device)), "qh_hull2d_batched")
+    return out, counts[:num_sets]
+
+
+def hull2d_host(points: np.ndarray, plan: Plan, out: np.ndarray | None = None) -> np.ndarray:
+    """End-to-end form with host buffers (copies inside the call); synchronizes."""
+    lib = load()
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    n = p.shape[0]
+    if out is None:
+        out = np.empty(max(n, 1), dtype=np.int32)
+    cnt = ctypes.c_int32(0)
+    _check(lib.qh_hull2d_host(plan.handle, p.ctypes.data, n, out.ctypes.data, ctypes.byref(cnt), _stream()),
+           "qh_hull2d_host")
+    return out[: cnt.value]
+
+
+def check_orient_host(tri: np.ndarray, prec: int = 0):
+    """Filtered orientation of triples (float32 [n, 6]) on the CPU: (sign, certified)."""
+    lib = load()
+    t = np.ascontiguousarray(tri, dtype=np.float32).reshape(-1, 6)
+    n = t.shape[0]
+    sign = np.zeros(n, dtype=np.int32)
+    cert = np.zeros(n, dtype=np.int32)
+    _check(lib.qh_check_orient_host(t.ctypes.data, n, int(prec), sign.ctypes.data, cert.ctypes.data),
+           "qh_check_orient_host")
+    return sign, cert
+
+
+def check_orient_device(tri, prec: int = 0):
+    import torch
+
+    lib = load()
+    t = tri.contiguous()
+    n = t.shape[0]
+    sign = torch.zeros(n, dtype=torch.int32, device=t.device)
+    cert = torch.zeros(n, dtype=torch.int32, device=t.device)
+    _check(lib.qh_check_orient_device(t.data_ptr(), n, int(prec), sign.data_ptr(), cert.data_ptr(),
+                                      _stream(t.device)), "qh_check_orient_device")
+    return sign, cert
+
+
+def check_dist_host(quads: np.ndarray):
+    lib = load()
+    q = np.ascontiguousarray(quads, dtype=np.float32).reshape(-1, 8)
+    sign = np.zeros(q.shape[0], dtype=np.int32)
+    _check(lib.qh_check_dist_host(q.ctypes.data, q.shape[0], sign.ctypes.data), "qh_check_dist_host")
+    return sign
+
+
+def check_dist_device(quads):
+    import torch
+
+    lib = load()
+    q = quads.contiguous()
+    sign = torch.zeros(q.shape[0], dtype=torch.int32, device=q.device)
+    _check(lib.qh_check_dist_device(q.data_ptr(), q.shape[0], sign.data_ptr(), _stream(q.device)),
+           "qh_check_dist_device")
+    return sign

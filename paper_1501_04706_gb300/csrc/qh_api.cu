@@ -1,0 +1,455 @@
+// C ABI of the hull library: plans (device scratch), the launch sequence and
+// statistics.  See include/qh.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/qh.h"
+#include "qh_internal.cuh"
+
+using namespace qh;
+
+struct qh_plan_s {
+    int device = 0;
+    long long ncap = 0;
+    int maxSets = 0;
+    unsigned flags = 0;
+    int cut = TILE;
+    int timing = 0;
+    int ctasPerSm = 0;
+    int numSMs = 0;
+    // device scratch
+    float2 *xy[2] = {nullptr, nullptr};
+    int *id[2] = {nullptr, nullptr};
+    int *vscratch = nullptr;
+    unsigned *tstatus = nullptr;
+    Carry *tagg = nullptr, *tinc = nullptr;
+    Ext *text = nullptr;
+    long long maxTiles = 0;
+    Inst *inst = nullptr;
+    int *bigInst = nullptr, *smallInst = nullptr;
+    long long *bigTilePrefix = nullptr;
+    Node *nodes = nullptr;
+    int maxNodes = 0;
+    int *bigList[2] = {nullptr, nullptr};
+    long long *vstart[2] = {nullptr, nullptr};
+    int maxBig = 0;
+    int *smallQ = nullptr;
+    Ctl *ctl = nullptr;
+    // host side
+    Ctl *hctl = nullptr;  // pinned
+    cudaStream_t last = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool evRecorded = false;
+    int lastSets = 0;
+    // end-to-end staging
+    float *stIn = nullptr;
+    int *stOut = nullptr;
+    int *stCnt = nullptr;
+    long long stCap = 0;
+};
+
+namespace {
+
+qh_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return QH_OK;
+    if (e == cudaErrorMemoryAllocation) return QH_ERR_OOM;
+    return QH_ERR_CUDA;
+}
+
+template <typename T> cudaError_t dalloc(T **p, long long count) {
+    if (count < 1) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+}
+
+void plan_free(qh_plan p) {
+    if (!p) return;
+    cudaFree(p->xy[0]);
+    cudaFree(p->xy[1]);
+    cudaFree(p->id[0]);
+    cudaFree(p->id[1]);
+    cudaFree(p->vscratch);
+    cudaFree(p->tstatus);
+    cudaFree(p->tagg);
+    cudaFree(p->tinc);
+    cudaFree(p->text);
+    cudaFree(p->inst);
+    cudaFree(p->bigInst);
+    cudaFree(p->smallInst);
+    cudaFree(p->bigTilePrefix);
+    cudaFree(p->nodes);
+    cudaFree(p->bigList[0]);
+    cudaFree(p->bigList[1]);
+    cudaFree(p->vstart[0]);
+    cudaFree(p->vstart[1]);
+    cudaFree(p->smallQ);
+    cudaFree(p->ctl);
+    cudaFree(p->stIn);
+    cudaFree(p->stOut);
+    cudaFree(p->stCnt);
+    if (p->hctl) cudaFreeHost(p->hctl);
+    for (auto &e : p->ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+qh_status plan_alloc(qh_plan p) {
+    const long long N = p->ncap;
+    cudaError_t e = cudaSuccess;
+#define QH_ALLOC(ptr, cnt)                   \
+    do {                                     \
+        e = dalloc(&(ptr), (cnt));           \
+        if (e != cudaSuccess) return cuda_status(e); \
+    } while (0)
+    QH_ALLOC(p->xy[0], 2 * N);
+    QH_ALLOC(p->xy[1], 2 * N);
+    QH_ALLOC(p->id[0], 2 * N);
+    QH_ALLOC(p->id[1], 2 * N);
+    QH_ALLOC(p->vscratch, 2 * N);
+    p->maxTiles = N / TILE + p->maxSets + 16;
+    QH_ALLOC(p->tstatus, p->maxTiles);
+    QH_ALLOC(p->tagg, p->maxTiles);
+    QH_ALLOC(p->tinc, p->maxTiles);
+    QH_ALLOC(p->text, p->maxTiles);
+    QH_ALLOC(p->inst, p->maxSets);
+    QH_ALLOC(p->bigInst, p->maxSets + 1);
+    QH_ALLOC(p->smallInst, p->maxSets + 1);
+    QH_ALLOC(p->bigTilePrefix, p->maxSets + 2);
+    // every big segment holds more than TILE points
+    p->maxBig = (int)(N / TILE + 16);
+    long long bigSets = N / FIN_MAX + 1;
+    if (bigSets > p->maxSets) bigSets = p->maxSets;
+    long long nodes = 4 * bigSets + 16ll * 2 * p->maxBig + 4096;
+    if (nodes > 0x7fffffffll) nodes = 0x7fffffffll;
+    p->maxNodes = (int)nodes;
+    QH_ALLOC(p->nodes, p->maxNodes);
+    QH_ALLOC(p->bigList[0], p->maxBig + 1);
+    QH_ALLOC(p->bigList[1], p->maxBig + 1);
+    QH_ALLOC(p->vstart[0], p->maxBig + 2);
+    QH_ALLOC(p->vstart[1], p->maxBig + 2);
+    QH_ALLOC(p->smallQ, p->maxNodes);
+    QH_ALLOC(p->ctl, 1);
+#undef QH_ALLOC
+    e = cudaMallocHost((void **)&p->hctl, sizeof(Ctl));
+    if (e != cudaSuccess) return cuda_status(e);
+    memset(p->hctl, 0, sizeof(Ctl));
+    for (auto &ev : p->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return QH_OK;
+}
+
+Params make_params(qh_plan pl, const float *points, const long long *offsets, long long nSingle, int numSets,
+                   int *outIdx, int *outCounts) {
+    Params p;
+    memset(&p, 0, sizeof(p));
+    p.pts = reinterpret_cast<const float2 *>(points);
+    p.offsets = offsets;
+    p.nSingle = nSingle;
+    p.numSets = numSets;
+    p.mode = (pl->flags & QH_MODE_CHORD) ? 1 : 0;
+    p.ncap = pl->ncap;
+    p.outIdx = outIdx;
+    p.outCounts = outCounts;
+    for (int b = 0; b < 2; b++) {
+        p.xy[b] = pl->xy[b];
+        p.id[b] = pl->id[b];
+        p.bigList[b] = pl->bigList[b];
+        p.vstart[b] = pl->vstart[b];
+    }
+    p.vscratch = pl->vscratch;
+    p.tstatus = pl->tstatus;
+    p.tagg = pl->tagg;
+    p.tinc = pl->tinc;
+    p.text = pl->text;
+    p.maxTiles = pl->maxTiles;
+    p.inst = pl->inst;
+    p.bigInst = pl->bigInst;
+    p.smallInst = pl->smallInst;
+    p.bigTilePrefix = pl->bigTilePrefix;
+    p.nodes = pl->nodes;
+    p.maxNodes = pl->maxNodes;
+    p.maxBig = pl->maxBig;
+    p.smallQ = pl->smallQ;
+    p.ctl = pl->ctl;
+    p.cut = pl->cut;
+    return p;
+}
+
+qh_status run(qh_plan pl, const float *points, const long long *offsets, long long nSingle, int numSets,
+              int *outIdx, int *outCounts, cudaStream_t s) {
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != pl->device) return QH_ERR_INVALID_ARG;
+    const int prec = (pl->flags & QH_PREC_F64) ? 1 : 0;
+    Params p = make_params(pl, points, offsets, nSingle, numSets, outIdx, outCounts);
+    cudaError_t e = cudaMemsetAsync(pl->ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->tstatus, 0, sizeof(unsigned) * (size_t)pl->maxTiles, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const bool tm = pl->timing != 0;
+    if (tm) cudaEventRecord(pl->ev[0], s);
+    int per = rounds_max_ctas_per_sm(prec);
+    if (pl->ctasPerSm > 0 && pl->ctasPerSm < per) per = pl->ctasPerSm;
+    if (per < 1) return QH_ERR_CUDA;
+    e = launch_rounds(p, prec, pl->numSMs * per, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tm) cudaEventRecord(pl->ev[1], s);
+    e = launch_finish(p, prec, pl->numSMs, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tm) cudaEventRecord(pl->ev[2], s);
+    e = launch_emit(p, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tm) cudaEventRecord(pl->ev[3], s);
+    e = launch_copy(p, pl->numSMs * 4, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tm) cudaEventRecord(pl->ev[4], s);
+    pl->evRecorded = tm;
+    pl->last = s;
+    pl->lastSets = numSets;
+    return QH_OK;
+}
+
+struct DefaultPlans {
+    std::mutex mu;
+    qh_plan plan[64] = {};
+};
+DefaultPlans &defaults() {
+    static DefaultPlans d;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t qh_version(void) { return 10000; }
+
+const char *qh_status_string(qh_status s) {
+    switch (s) {
+    case QH_OK: return "ok";
+    case QH_ERR_INVALID_ARG: return "invalid argument";
+    case QH_ERR_NONFINITE: return "non-finite input coordinate";
+    case QH_ERR_CUDA: return "CUDA runtime error";
+    case QH_ERR_OOM: return "out of device memory";
+    case QH_ERR_CAPACITY: return "capacity exceeded";
+    case QH_ERR_TIMEOUT: return "device-side wait timed out";
+    case QH_ERR_INTERNAL: return "internal error";
+    case QH_ERR_UNSUPPORTED: return "unsupported in this context";
+    }
+    return "unknown status";
+}
+
+qh_status qh_plan_create(int64_t max_points, int32_t max_sets, uint32_t flags, qh_plan *out) {
+    if (!out || max_points < 1 || max_sets < 1 || (flags & ~3u)) return QH_ERR_INVALID_ARG;
+    if (max_points > (1ll << 30)) return QH_ERR_CAPACITY;  // indices are int32, nested ranges 2x
+    *out = nullptr;
+    qh_plan p = new (std::nothrow) qh_plan_s();
+    if (!p) return QH_ERR_OOM;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->numSMs, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_status(e);
+    }
+    p->ncap = max_points;
+    p->maxSets = max_sets;
+    p->flags = flags;
+    p->cut = FIN_MAX;
+    qh_status st = plan_alloc(p);
+    if (st != QH_OK) {
+        plan_free(p);
+        return st;
+    }
+    *out = p;
+    return QH_OK;
+}
+
+qh_status qh_plan_destroy(qh_plan plan) {
+    if (!plan) return QH_OK;
+    cudaDeviceSynchronize();
+    plan_free(plan);
+    return QH_OK;
+}
+
+qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags) {
+    if (!plan || (flags & ~3u)) return QH_ERR_INVALID_ARG;
+    plan->flags = flags;
+    return QH_OK;
+}
+
+qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int32_t grid_ctas_per_sm) {
+    if (!plan || cutover < TILE || cutover > FIN_MAX || grid_ctas_per_sm < 0) return QH_ERR_INVALID_ARG;
+    plan->cut = cutover;
+    plan->timing = timing ? 1 : 0;
+    plan->ctasPerSm = grid_ctas_per_sm;
+    return QH_OK;
+}
+
+qh_status qh_hull2d_p(qh_plan plan, const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                      qh_stream_t stream) {
+    if (!plan || n < 0 || !out_count || (n > 0 && (!points || !out_idx))) return QH_ERR_INVALID_ARG;
+    if (((uintptr_t)points & 7u) != 0) return QH_ERR_INVALID_ARG;
+    if (n > plan->ncap) return QH_ERR_CAPACITY;
+    return run(plan, points, nullptr, n, 1, out_idx, out_count, (cudaStream_t)stream);
+}
+
+qh_status qh_hull2d(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count, qh_stream_t stream) {
+    if (n < 0 || !out_count || (n > 0 && (!points || !out_idx))) return QH_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return QH_ERR_INVALID_ARG;
+    DefaultPlans &d = defaults();
+    std::lock_guard<std::mutex> lock(d.mu);
+    qh_plan &pl = d.plan[dev];
+    if (!pl || pl->ncap < n) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+        if (cs != cudaStreamCaptureStatusNone) return QH_ERR_UNSUPPORTED;
+        long long cap = n < (1 << 20) ? (1 << 20) : n;
+        if (pl) {
+            if (cap < 2 * pl->ncap) cap = 2 * pl->ncap;
+            if (cap > (1ll << 30)) cap = n;
+            qh_plan_destroy(pl);
+            pl = nullptr;
+        }
+        qh_status st = qh_plan_create(cap, 1, QH_MODE_QUAD | QH_PREC_F32, &pl);
+        if (st != QH_OK) {
+            pl = nullptr;
+            return st;
+        }
+    }
+    return qh_hull2d_p(pl, points, n, out_idx, out_count, stream);
+}
+
+qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *offsets, int32_t num_sets,
+                            int32_t *out_idx, int32_t *out_counts, qh_stream_t stream) {
+    if (!plan || num_sets < 0 || (num_sets > 0 && (!offsets || !out_counts || !points || !out_idx)))
+        return QH_ERR_INVALID_ARG;
+    if (((uintptr_t)points & 7u) != 0) return QH_ERR_INVALID_ARG;
+    if (num_sets > plan->maxSets) return QH_ERR_CAPACITY;
+    if (num_sets == 0) return QH_OK;
+    return run(plan, points, reinterpret_cast<const long long *>(offsets), 0, num_sets, out_idx, out_counts,
+               (cudaStream_t)stream);
+}
+
+qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
+                         int32_t *host_out_count, qh_stream_t stream) {
+    if (!plan || n < 0 || !host_out_count || (n > 0 && (!host_points || !host_out_idx))) return QH_ERR_INVALID_ARG;
+    if (n > plan->ncap) return QH_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->stCap < n || !plan->stIn) {
+        cudaStreamSynchronize(s);
+        cudaFree(plan->stIn);
+        cudaFree(plan->stOut);
+        cudaFree(plan->stCnt);
+        plan->stIn = nullptr;
+        plan->stOut = nullptr;
+        plan->stCnt = nullptr;
+        long long cap = n < 1024 ? 1024 : n;
+        cudaError_t e = cudaMalloc((void **)&plan->stIn, sizeof(float) * 2 * (size_t)cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stOut, sizeof(int) * (size_t)cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stCnt, sizeof(int));
+        if (e != cudaSuccess) return cuda_status(e);
+        plan->stCap = cap;
+    }
+    cudaError_t e = cudaMemcpyAsync(plan->stIn, host_points, sizeof(float) * 2 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    qh_status st = qh_hull2d_p(plan, plan->stIn, n, plan->stOut, plan->stCnt, stream);
+    if (st != QH_OK) return st;
+    e = cudaMemcpyAsync(host_out_count, plan->stCnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int h = *host_out_count;
+    if (h > 0) {
+        e = cudaMemcpyAsync(host_out_idx, plan->stOut, sizeof(int) * (size_t)h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+    } else if (h < 0) {
+        return (qh_status)(-h);
+    }
+    return QH_OK;
+}
+
+qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
+    if (!plan || !out) return QH_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(plan->last);
+    if (e == cudaSuccess) e = cudaMemcpy(plan->hctl, plan->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    const Ctl &c = *plan->hctl;
+    memset(out, 0, sizeof(*out));
+    unsigned err = c.err;
+    out->device_status = err == 0u ? 0 : (err & E_ARG) ? QH_ERR_INVALID_ARG : (err & E_TIMEOUT) ? QH_ERR_TIMEOUT
+                                     : (err & E_CAPACITY) ? QH_ERR_CAPACITY : QH_ERR_INTERNAL;
+    out->global_rounds = c.rounds;
+    out->small_problems = c.nSmall + c.nSmallInst;
+    out->nodes = c.nNodes;
+    out->big_sets = c.nBig;
+    int last = -1;
+    for (int g = 0; g < QH_MAX_GEN && g < MAX_GEN; g++) {
+        out->live[g] = c.live[g];
+        if (c.live[g] > 0) last = g;
+    }
+    out->generations = last < 0 ? 1 : last + 2;
+    out->exact_orient = (int64_t)c.exactOrient;
+    out->exact_compare = (int64_t)c.exactCmp;
+    if (plan->evRecorded) {
+        for (int k = 0; k < 4; k++) cudaEventElapsedTime(&out->phase_ms[k], plan->ev[k], plan->ev[k + 1]);
+        cudaEventElapsedTime(&out->phase_ms[4], plan->ev[0], plan->ev[4]);
+    }
+    return QH_OK;
+}
+
+// ------------------------------------------------------------------------
+// predicate check hooks
+// ------------------------------------------------------------------------
+qh_status qh_check_orient_host(const float *tri, int64_t n, int32_t prec, int32_t *sign, int32_t *certified) {
+    if (n < 0 || (n > 0 && (!tri || !sign || !certified))) return QH_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n; k++) {
+        const float *t = tri + 6 * k;
+        int used = 0;
+        if (prec) {
+            const Edge<double> e = make_edge<double>(t[0], t[1], t[2], t[3]);
+            sign[k] = orient_sign(e, t[2], t[3], t[4], t[5], orient_approx(e, t[4], t[5]), used);
+        } else {
+            const Edge<float> e = make_edge<float>(t[0], t[1], t[2], t[3]);
+            sign[k] = orient_sign(e, t[2], t[3], t[4], t[5], orient_approx(e, t[4], t[5]), used);
+        }
+        certified[k] = used == 0;
+    }
+    return QH_OK;
+}
+
+qh_status qh_check_orient_device(const float *tri, int64_t n, int32_t prec, int32_t *sign, int32_t *certified,
+                                 qh_stream_t stream) {
+    if (n < 0 || (n > 0 && (!tri || !sign || !certified))) return QH_ERR_INVALID_ARG;
+    return cuda_status(launch_check_orient(tri, n, prec, sign, certified, (cudaStream_t)stream));
+}
+
+qh_status qh_check_dist_host(const float *quads, int64_t n, int32_t *sign) {
+    if (n < 0 || (n > 0 && (!quads || !sign))) return QH_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n; k++) {
+        const float *t = quads + 8 * k;
+        const Edge<float> e = make_edge<float>(t[0], t[1], t[2], t[3]);
+        const DistIv<float> a = dist_interval(orient_approx(e, t[4], t[5]));
+        const DistIv<float> b = dist_interval(orient_approx(e, t[6], t[7]));
+        if (a.lo > b.hi)
+            sign[k] = 1;
+        else if (b.lo > a.hi)
+            sign[k] = -1;
+        else
+            sign[k] = dist_cmp_exact(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7]);
+    }
+    return QH_OK;
+}
+
+qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_stream_t stream) {
+    if (n < 0 || (n > 0 && (!quads || !sign))) return QH_ERR_INVALID_ARG;
+    return cuda_status(launch_check_dist(quads, n, sign, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,652 @@
+// Block-level parts of segmented QuickHull.
+//
+// finish_kernel  one thread block per small problem: a segment of at most
+//                `cut` points left by the grid-wide rounds, or a whole set of at
+//                most FIN_MAX points.  The block runs the remaining generations
+//                of Sec. 4.4 with all state in shared memory: per point the id
+//                of its segment; per live segment its place in the CCW list of
+//                segment heads; per generation the farthest point of each new
+//                segment and the classification against the two new edges.
+// emit_kernel    one block per set: walks the binary tree of segments built by
+//                the grid-wide rounds (each big segment (h, e) split at its
+//                farthest point c into (h, c), (c, e)), computes the output
+//                offset of every leaf in CCW order, and writes the heads.
+// copy_kernel    copies the inner vertices found by the finisher to their
+//                output offsets.
+#include "qh_internal.cuh"
+
+namespace qh {
+
+constexpr int FM = FIN_MAX;
+constexpr unsigned short NONE16 = 0xffffu;
+
+struct OrdE {
+    unsigned short head, live, c, pad;  // head point, live segment id (or NONE16), its farthest point
+};
+
+struct FinSmem {
+    float2 pxy[FM + 2];
+    unsigned short seg[FM];  // per point: live segment / child code, NONE16 = discarded
+    OrdE ordA[FM + 8], ordB[FM + 8];
+    unsigned short lpos[FM];  // live segment -> position in the ord list
+    unsigned cnt2[FM];        // per live segment: packed child counts (low: first child, high: second)
+    unsigned maxLo[2 * FM];   // per child: largest lower distance bound (orderable key)
+    unsigned short best[2 * FM];
+    unsigned short newId[2 * FM];
+    int scan[FIN_NT / 32 + 1];
+    int ticket, cLocal, nOrd, S, K, degenerate, nonfinite;
+    long long liveCount;
+    unsigned short poly[4];
+    Ext wext[FIN_NT / 32];
+};
+
+__device__ __forceinline__ Cand shfl_c(const Cand &c, int src) {
+    Cand o;
+    o.x = __shfl_sync(0xffffffffu, c.x, src);
+    o.y = __shfl_sync(0xffffffffu, c.y, src);
+    o.idx = __shfl_sync(0xffffffffu, c.idx, src);
+    o.pad = 0;
+    return o;
+}
+
+__device__ __forceinline__ void ext_merge_f(Ext &a, const Ext &b) {
+    if (lex_less(b.a.x, b.a.y, b.a.idx, a.a.x, a.a.y, a.a.idx)) a.a = b.a;
+    if (lex_greater(b.b.x, b.b.y, b.b.idx, a.b.x, a.b.y, a.b.idx)) a.b = b.b;
+    if (lex_less(b.bot.y, b.bot.x, b.bot.idx, a.bot.y, a.bot.x, a.bot.idx)) a.bot = b.bot;
+    if (lex_greater(b.top.y, b.top.x, b.top.idx, a.top.y, a.top.x, a.top.idx)) a.top = b.top;
+    a.nonfinite |= b.nonfinite;
+}
+
+// Chord (u, v) of child c: initial edges of the polygon, or the two edges
+// (h, C), (C, e) of live segment c >> 1.
+__device__ __forceinline__ void child_chord(const FinSmem &s, const OrdE *ord, int nOrd, bool initial, int c, int &u,
+                                            int &v) {
+    if (initial) {
+        u = s.poly[c];
+        v = s.poly[(c + 1) % s.K];
+    } else {
+        const int pos = s.lpos[c >> 1];
+        const OrdE &o = ord[pos];
+        if (c & 1) {
+            u = o.c;
+            v = ord[(pos + 1) % nOrd].head;
+        } else {
+            u = o.head;
+            v = o.c;
+        }
+    }
+}
+
+template <typename P>
+__device__ __forceinline__ bool fin_right_of(const FinSmem &s, int u, int v, float px, float py, P &lo, P &hi,
+                                             int &exact_o) {
+    const float2 a = s.pxy[u], b = s.pxy[v];
+    const Edge<P> e = make_edge<P>(a.x, a.y, b.x, b.y);
+    Approx<P> o = orient_approx(e, px, py);
+    if (orient_sign(e, b.x, b.y, px, py, o, exact_o) < 0) {
+        DistIv<P> d = dist_interval(o);
+        lo = d.lo;
+        hi = d.hi;
+        return true;
+    }
+    return false;
+}
+
+// One generation.  Classification (pass 1), exact farthest point per child
+// (pass 2), rebuild of the CCW head list and of the live segments, relabelling.
+template <typename P>
+__device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial, OrdE *&ord, OrdE *&ordN,
+                               const int *gidx, int gen, int &exact_o, int &exact_c) {
+    const int S = s.S, nOrd = s.nOrd;
+    const int nch = initial ? s.K : 2 * S;
+    for (int c = threadIdx.x; c < nch; c += FIN_NT) {
+        s.maxLo[c] = 0u;
+        s.best[c] = NONE16;
+    }
+    for (int j = threadIdx.x; j < (initial ? s.K : S); j += FIN_NT) s.cnt2[j] = 0u;
+    __syncthreads();
+    // pass 1: classify
+    for (int k = threadIdx.x; k < m; k += FIN_NT) {
+        const unsigned short j = s.seg[k];
+        if (j == NONE16) continue;
+        const float2 q = s.pxy[k];
+        P lo = P(0), hi = P(0);
+        int child = -1;
+        if (initial) {
+            for (int c = 0; c < s.K; c++) {
+                int u, v;
+                child_chord(s, ord, nOrd, true, c, u, v);
+                if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
+                    child = c;
+                    break;
+                }
+            }
+        } else {
+            int u, v;
+            child_chord(s, ord, nOrd, false, 2 * j, u, v);
+            if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
+                child = 2 * j;
+            } else {
+                child_chord(s, ord, nOrd, false, 2 * j + 1, u, v);
+                if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) child = 2 * j + 1;
+            }
+        }
+        if (child < 0) {
+            s.seg[k] = NONE16;
+            continue;
+        }
+        s.seg[k] = (unsigned short)child;
+        if (initial)
+            atomicAdd(&s.cnt2[child], 1u);
+        else
+            atomicAdd(&s.cnt2[child >> 1], (child & 1) ? 0x10000u : 1u);
+        atomicMax(&s.maxLo[child], max(pkey(lo), 1u));
+    }
+    __syncthreads();
+    // pass 2: exact farthest point among the candidates of each child
+    for (int k = threadIdx.x; k < m; k += FIN_NT) {
+        const unsigned short c = s.seg[k];
+        if (c == NONE16) continue;
+        int u, v;
+        child_chord(s, ord, nOrd, initial, c, u, v);
+        const float2 a = s.pxy[u], b = s.pxy[v];
+        const Edge<P> e = make_edge<P>(a.x, a.y, b.x, b.y);
+        const float2 q = s.pxy[k];
+        DistIv<P> dq = dist_interval(orient_approx(e, q.x, q.y));
+        const P thr = (P)fkey_inv(s.maxLo[c]);
+        if (!(dq.hi >= thr)) continue;
+        const int qi = gidx ? __ldg(&gidx[k]) : k;
+        unsigned short cur = s.best[c];
+        for (int it = 0; it < 1 << 20; it++) {
+            bool mine;
+            if (cur == NONE16) {
+                mine = true;
+            } else {
+                const float2 w = s.pxy[cur];
+                const int wi = gidx ? __ldg(&gidx[cur]) : (int)cur;
+                DistIv<P> dw = dist_interval(orient_approx(e, w.x, w.y));
+                mine = farther(e, b.x, b.y, q.x, q.y, qi, dq, w.x, w.y, wi, dw, exact_c);
+            }
+            if (!mine) break;
+            const unsigned short prev = atomicCAS(&s.best[c], cur, (unsigned short)k);
+            if (prev == cur) break;
+            cur = prev;
+        }
+    }
+    __syncthreads();
+    // children that hold points become the new live segments
+    {
+        const int per = (nch + FIN_NT - 1) / FIN_NT;
+        const int b = min(nch, (int)threadIdx.x * per), e = min(nch, b + per);
+        int has = 0;
+        long long pts = 0;
+        for (int c = b; c < e; c++) {
+            const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
+            has += cnt > 0u;
+            pts += cnt;
+        }
+        int tot;
+        int x = block_excl_scan<int, FIN_NT>(has, s.scan, tot);
+        for (int c = b; c < e; c++) {
+            const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
+            s.newId[c] = cnt > 0u ? (unsigned short)(x++) : NONE16;
+        }
+        if (threadIdx.x == 0) {
+            s.S = tot;
+            s.liveCount = 0;
+        }
+        __syncthreads();
+        if (pts) atomicAdd((unsigned long long *)&s.liveCount, (unsigned long long)pts);
+    }
+    __syncthreads();
+    // new CCW list of heads
+    if (initial) {
+        for (int c = threadIdx.x; c < s.K; c += FIN_NT) {
+            OrdE o;
+            o.head = s.poly[c];
+            o.live = s.newId[c];
+            o.c = o.live != NONE16 ? s.best[c] : NONE16;
+            o.pad = 0;
+            ordN[c] = o;
+            if (o.live != NONE16) s.lpos[o.live] = (unsigned short)c;
+        }
+        if (threadIdx.x == 0) s.nOrd = s.K;
+    } else {
+        const int per = (nOrd + FIN_NT - 1) / FIN_NT;
+        const int b = min(nOrd, (int)threadIdx.x * per), e = min(nOrd, b + per);
+        int w = 0;
+        for (int q = b; q < e; q++) w += ord[q].live != NONE16 ? 2 : 1;
+        int tot;
+        int np = block_excl_scan<int, FIN_NT>(w, s.scan, tot);
+        if (tot > FM + 4) {  // guard: at most one head per point plus the chord ends
+            if (threadIdx.x == 0) {
+                set_err(p.ctl, E_INTERNAL);
+                s.S = 0;
+                s.nOrd = 0;
+            }
+            __syncthreads();
+            return;
+        }
+        for (int q = b; q < e; q++) {
+            const OrdE o = ord[q];
+            if (o.live == NONE16) {
+                ordN[np++] = o;
+                continue;
+            }
+            const int j = o.live;
+            for (int wch = 0; wch < 2; wch++) {
+                OrdE n;
+                n.head = wch ? o.c : o.head;
+                n.live = s.newId[2 * j + wch];
+                n.c = n.live != NONE16 ? s.best[2 * j + wch] : NONE16;
+                n.pad = 0;
+                ordN[np] = n;
+                if (n.live != NONE16) s.lpos[n.live] = (unsigned short)np;
+                np++;
+            }
+        }
+        if (threadIdx.x == 0) s.nOrd = tot;
+    }
+    __syncthreads();
+    // relabel points with their new live segment
+    for (int k = threadIdx.x; k < m; k += FIN_NT) {
+        const unsigned short c = s.seg[k];
+        if (c != NONE16) s.seg[k] = s.newId[c];
+    }
+    if (threadIdx.x == 0)
+        atomicAdd((unsigned long long *)&p.ctl->live[min(gen, MAX_GEN - 1)], (unsigned long long)s.liveCount);
+    OrdE *t = ord;
+    ord = ordN;
+    ordN = t;
+    __syncthreads();
+}
+
+template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, bool isNode, int id, int &exact_o,
+                                                int &exact_c) {
+    int m;
+    const float2 *src;
+    const int *gidx = nullptr;
+    long long outOff = 0;
+    int gen = 0;
+    Cand H = no_cand(), E = no_cand(), C = no_cand();
+    long long pstart = 0;
+    if (isNode) {
+        const Node *N = &p.nodes[id];
+        m = N->count;
+        const int buf = N->buf;
+        pstart = N->pstart;
+        src = p.xy[buf] + pstart;
+        gidx = p.id[buf] + pstart;
+        gen = N->level + 1;
+        H = N->h;
+        E = N->e;
+        C = N->c;
+    } else {
+        const Inst *I = &p.inst[id];
+        m = (int)I->n;
+        outOff = I->off;
+        src = p.pts + I->off;
+    }
+    if (m < 1 || m > FM) {  // guard: shared-memory tables hold FIN_MAX points
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        s.cLocal = -1;
+        s.nonfinite = 0;
+        s.degenerate = 0;
+    }
+    __syncthreads();
+    Ext ex;
+    ex.a = ex.b = ex.bot = ex.top = no_cand();
+    ex.nonfinite = 0;
+    for (int k = threadIdx.x; k < m; k += FIN_NT) {
+        const float2 q = __ldg(&src[k]);
+        s.pxy[k] = q;
+        if (isNode) {
+            s.seg[k] = 0;
+            if (__ldg(&gidx[k]) == C.idx) s.cLocal = k;
+        } else {
+            if (!isfinite(q.x) || !isfinite(q.y)) {
+                ex.nonfinite = 1;
+            } else {
+                if (lex_less(q.x, q.y, k, ex.a.x, ex.a.y, ex.a.idx)) ex.a = mk_cand(q.x, q.y, k);
+                if (lex_greater(q.x, q.y, k, ex.b.x, ex.b.y, ex.b.idx)) ex.b = mk_cand(q.x, q.y, k);
+                if (lex_less(q.y, q.x, k, ex.bot.y, ex.bot.x, ex.bot.idx)) ex.bot = mk_cand(q.x, q.y, k);
+                if (lex_greater(q.y, q.x, k, ex.top.y, ex.top.x, ex.top.idx)) ex.top = mk_cand(q.x, q.y, k);
+            }
+            s.seg[k] = 0;
+        }
+    }
+    OrdE *ord = s.ordA, *ordN = s.ordB;
+    if (isNode) {
+        if (threadIdx.x == 0) {
+            s.pxy[m] = make_float2(H.x, H.y);
+            s.pxy[m + 1] = make_float2(E.x, E.y);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s.cLocal < 0) set_err(p.ctl, E_INTERNAL);
+            OrdE a, b;
+            a.head = (unsigned short)m;
+            a.live = 0;
+            a.c = (unsigned short)max(s.cLocal, 0);
+            a.pad = 0;
+            b.head = (unsigned short)(m + 1);
+            b.live = NONE16;
+            b.c = NONE16;
+            b.pad = 0;
+            ord[0] = a;
+            ord[1] = b;
+            s.lpos[0] = 0;
+            s.nOrd = 2;
+            s.S = 1;
+        }
+        __syncthreads();
+        if (s.cLocal < 0) return;
+    } else {
+        // extreme points of the set (Sec. 4.2) and the initial polygon
+        for (int d = 16; d >= 1; d >>= 1) {
+            Ext o;
+            const int l = (threadIdx.x & 31) ^ d;
+            o.a = shfl_c(ex.a, l);
+            o.b = shfl_c(ex.b, l);
+            o.bot = shfl_c(ex.bot, l);
+            o.top = shfl_c(ex.top, l);
+            o.nonfinite = __shfl_sync(0xffffffffu, ex.nonfinite, l);
+            ext_merge_f(ex, o);
+        }
+        if ((threadIdx.x & 31) == 0) s.wext[threadIdx.x >> 5] = ex;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Ext a = s.wext[0];
+            for (int w = 1; w < FIN_NT / 32; w++) ext_merge_f(a, s.wext[w]);
+            int K = 0;
+            if (a.nonfinite) {
+                s.nonfinite = 1;
+            } else if (a.a.x == a.b.x && a.a.y == a.b.y) {
+                s.degenerate = 1;
+                s.poly[0] = (unsigned short)a.a.idx;
+            } else {
+                const bool quad = (p.mode == 0);
+                s.poly[K++] = (unsigned short)a.a.idx;
+                if (quad && !(a.bot.x == a.a.x && a.bot.y == a.a.y) && !(a.bot.x == a.b.x && a.bot.y == a.b.y))
+                    s.poly[K++] = (unsigned short)a.bot.idx;
+                s.poly[K++] = (unsigned short)a.b.idx;
+                if (quad && !(a.top.x == a.a.x && a.top.y == a.a.y) && !(a.top.x == a.b.x && a.top.y == a.b.y))
+                    s.poly[K++] = (unsigned short)a.top.idx;
+            }
+            s.K = K;
+            s.S = 0;
+            s.nOrd = 0;
+        }
+        __syncthreads();
+        if (s.nonfinite) {
+            if (threadIdx.x == 0) p.outCounts[id] = -2;
+            return;
+        }
+        if (s.degenerate) {
+            if (threadIdx.x == 0) {
+                p.outIdx[outOff] = s.poly[0];
+                p.outCounts[id] = 1;
+            }
+            return;
+        }
+        fin_generation<P>(p, s, m, true, ord, ordN, nullptr, 0, exact_o, exact_c);
+        gen = 1;
+    }
+    const int genLimit = gen + m + 4;  // every generation removes at least one point per live segment
+    while (s.S > 0) {
+        if (gen > genLimit || ld_volatile(&p.ctl->err) != 0u) {
+            if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+            return;
+        }
+        fin_generation<P>(p, s, m, false, ord, ordN, gidx, gen, exact_o, exact_c);
+        gen++;
+    }
+    const int nOrd = s.nOrd;
+    if (nOrd > m + (isNode ? 2 : 0)) {  // guard: the output never exceeds the problem's points
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        __syncthreads();
+        return;
+    }
+    if (isNode) {
+        // heads strictly between h (entry 0) and e (last entry)
+        for (int q = 1 + threadIdx.x; q < nOrd - 1; q += FIN_NT) p.vscratch[pstart + q - 1] = __ldg(&gidx[ord[q].head]);
+        if (threadIdx.x == 0) p.nodes[id].inner = nOrd - 2;
+    } else {
+        for (int q = threadIdx.x; q < nOrd; q += FIN_NT) p.outIdx[outOff + q] = ord[q].head;
+        if (threadIdx.x == 0) p.outCounts[id] = nOrd;
+    }
+    __syncthreads();
+}
+
+template <typename P> __global__ void __launch_bounds__(FIN_NT, 1) finish_kernel(Params p) {
+    extern __shared__ __align__(16) unsigned char fin_smem_raw[];
+    FinSmem &s = *reinterpret_cast<FinSmem *>(fin_smem_raw);
+    if (p.ctl->err != 0u) return;
+    const int nSI = p.ctl->nSmallInst, nSN = p.ctl->nSmall;
+    int exact_o = 0, exact_c = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s.ticket = (int)atomicAdd(&p.ctl->finTicket, 1u);
+        __syncthreads();
+        const int w = s.ticket;
+        __syncthreads();
+        if (w >= nSI + nSN) break;
+        if (w < nSI)
+            fin_solve<P>(p, s, false, p.smallInst[w], exact_o, exact_c);
+        else
+            fin_solve<P>(p, s, true, p.smallQ[w - nSI], exact_o, exact_c);
+    }
+    unsigned long long eo = (unsigned long long)exact_o, ec = (unsigned long long)exact_c;
+    for (int d = 16; d >= 1; d >>= 1) {
+        eo += __shfl_xor_sync(0xffffffffu, eo, d);
+        ec += __shfl_xor_sync(0xffffffffu, ec, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (eo) atomicAdd(&p.ctl->exactOrient, eo);
+        if (ec) atomicAdd(&p.ctl->exactCmp, ec);
+    }
+}
+
+// --------------------------------------------------------------------------
+// emit: output offsets of the segment tree of every big set
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int status_of(unsigned err) {
+    if (err & E_ARG) return 1;
+    if (err & E_TIMEOUT) return 6;
+    if (err & E_CAPACITY) return 5;
+    return 7;
+}
+
+constexpr int EMIT_NT = 256;
+
+__global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
+    __shared__ int lo_s[MAX_LEVELS + 1], hi_s[MAX_LEVELS + 1];
+    const int i = blockIdx.x;
+    if (i >= p.numSets) return;
+    const unsigned err = p.ctl->err;
+    if (err != 0u) {
+        if (threadIdx.x == 0) p.outCounts[i] = -status_of(err);
+        return;
+    }
+    const Inst *I = &p.inst[i];
+    const int kind = I->kind;
+    if (kind == I_EMPTY || kind == I_SMALL) return;
+    if (kind == I_NONFINITE) {
+        if (threadIdx.x == 0) p.outCounts[i] = -2;
+        return;
+    }
+    const long long off = I->off;
+    if (kind == I_DEGEN) {
+        if (threadIdx.x == 0) {
+            p.outIdx[off] = I->poly[0].idx;
+            p.outCounts[i] = 1;
+        }
+        return;
+    }
+    const int nL = p.ctl->nLevels;
+    const int K = I->K;
+    // node range of this set in every level (levels are grouped by set, in set order)
+    for (int r = threadIdx.x; r < nL; r += EMIT_NT) {
+        const int a = p.ctl->levelBase[r], b = p.ctl->levelBase[r + 1];
+        if (r == 0) {
+            lo_s[0] = I->level0;
+            hi_s[0] = I->level0 + K;
+            continue;
+        }
+        int l = a, h = b;
+        while (l < h) {
+            int mid = (l + h) >> 1;
+            if (p.nodes[mid].inst < i) l = mid + 1; else h = mid;
+        }
+        int l2 = l, h2 = b;
+        while (l2 < h2) {
+            int mid = (l2 + h2) >> 1;
+            if (p.nodes[mid].inst <= i) l2 = mid + 1; else h2 = mid;
+        }
+        lo_s[r] = l;
+        hi_s[r] = l2;
+    }
+    __syncthreads();
+    for (int r = nL - 1; r >= 0; r--) {
+        for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
+            Node *N = &p.nodes[q];
+            int vc;
+            if (N->kind == K_LEAF)
+                vc = 1;
+            else if (N->kind == K_SMALL)
+                vc = 1 + N->inner;
+            else if (N->child >= 0 && N->child + 1 < p.maxNodes)
+                vc = p.nodes[N->child].vc + p.nodes[N->child + 1].vc;
+            else {
+                set_err(p.ctl, E_INTERNAL);
+                vc = 0;
+            }
+            N->vc = vc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int k = 0; k < K; k++) {
+            Node *N = &p.nodes[I->level0 + k];
+            N->off = o;
+            o += N->vc;
+        }
+        p.outCounts[i] = (int)o;
+    }
+    __syncthreads();
+    for (int r = 0; r < nL; r++) {
+        for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
+            Node *N = &p.nodes[q];
+            if (N->kind == K_BIG) {
+                if (N->child < 0 || N->child + 1 >= p.maxNodes) continue;
+                Node *A = &p.nodes[N->child];
+                Node *B = &p.nodes[N->child + 1];
+                A->off = N->off;
+                B->off = N->off + A->vc;
+            } else if (N->off >= 0 && N->off < I->n) {
+                p.outIdx[off + N->off] = N->h.idx;
+            } else {
+                set_err(p.ctl, E_INTERNAL);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void copy_kernel(Params p) {
+    if (p.ctl->err != 0u) return;
+    const int nSN = p.ctl->nSmall;
+    for (int w = blockIdx.x; w < nSN; w += gridDim.x) {
+        const Node *N = &p.nodes[p.smallQ[w]];
+        const int inner = N->inner;
+        if (N->off < 0 || N->off + 1 + inner > p.inst[N->inst].n || inner > N->count) {
+            if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+            continue;
+        }
+        int *dst = p.outIdx + p.inst[N->inst].off + N->off + 1;
+        const int *src = p.vscratch + N->pstart;
+        for (int k = threadIdx.x; k < inner; k += blockDim.x) dst[k] = src[k];
+    }
+}
+
+// --------------------------------------------------------------------------
+// predicate check kernels
+// --------------------------------------------------------------------------
+template <typename P> __global__ void check_orient_kernel(const float *tri, long long n, int *sign, int *cert) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float *t = tri + 6 * k;
+    const Edge<P> e = make_edge<P>(t[0], t[1], t[2], t[3]);
+    const Approx<P> o = orient_approx(e, t[4], t[5]);
+    int used = 0;
+    sign[k] = orient_sign(e, t[2], t[3], t[4], t[5], o, used);
+    cert[k] = used == 0;
+}
+
+__global__ void check_dist_kernel(const float *q, long long n, int *sign) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float *t = q + 8 * k;
+    const Edge<float> e = make_edge<float>(t[0], t[1], t[2], t[3]);
+    const DistIv<float> a = dist_interval(orient_approx(e, t[4], t[5]));
+    const DistIv<float> b = dist_interval(orient_approx(e, t[6], t[7]));
+    int s;
+    if (a.lo > b.hi)
+        s = 1;
+    else if (b.lo > a.hi)
+        s = -1;
+    else
+        s = dist_cmp_exact(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7]);
+    sign[k] = s;
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+int finish_smem_bytes() { return (int)sizeof(FinSmem); }
+
+cudaError_t launch_finish(const Params &p, int prec, int grid, cudaStream_t s) {
+    const int bytes = finish_smem_bytes();
+    cudaError_t e;
+    if (prec) {
+        e = cudaFuncSetAttribute(finish_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        finish_kernel<double><<<grid, FIN_NT, bytes, s>>>(p);
+    } else {
+        e = cudaFuncSetAttribute(finish_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        finish_kernel<float><<<grid, FIN_NT, bytes, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const Params &p, cudaStream_t s) {
+    if (p.numSets > 0) emit_kernel<<<p.numSets, EMIT_NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const Params &p, int grid, cudaStream_t s) {
+    copy_kernel<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_orient(const float *tri, long long n, int prec, int *sign, int *cert, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (int)((n + 255) / 256);
+    if (prec)
+        check_orient_kernel<double><<<nb, 256, 0, s>>>(tri, n, sign, cert);
+    else
+        check_orient_kernel<float><<<nb, 256, 0, s>>>(tri, n, sign, cert);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_dist(const float *quads, long long n, int *sign, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    check_dist_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(quads, n, sign);
+    return cudaGetLastError();
+}
+
+}  // namespace qh

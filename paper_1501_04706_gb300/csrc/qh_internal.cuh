@@ -1,0 +1,270 @@
+// Shared definitions of the hull kernels: tunables, device-side records, the
+// launch parameter block, and synchronisation helpers (bounded grid barrier,
+// acquire/release flags, block scans).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qh_predicates.cuh"
+
+namespace qh {
+
+// ---------------------------------------------------------------------------
+// Tunables
+// ---------------------------------------------------------------------------
+constexpr int NT = 512;            // threads per CTA of the grid-wide kernel
+constexpr int NWARP = NT / 32;
+constexpr int IPT = 4;             // points per thread per tile (warp-striped rows)
+constexpr int TILE = NT * IPT;     // points per tile
+constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
+constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
+constexpr int MAX_LEVELS = 48;     // grid-wide rounds (deeper recursions report QH_ERR_CAPACITY)
+constexpr int MAX_GEN = 64;        // generations tracked in the statistics
+constexpr unsigned SPIN_LIMIT = 1u << 22;  // polls (with back-off) before a wait gives up
+
+// device-side error bits (ctl->err)
+enum : unsigned { E_TIMEOUT = 1u, E_CAPACITY = 2u, E_INTERNAL = 4u, E_ARG = 8u };
+
+// instance kinds
+enum : int { I_EMPTY = 0, I_SMALL = 1, I_BIG = 2, I_DEGEN = 3, I_NONFINITE = 4 };
+// segment (node) kinds
+enum : int { K_LEAF = 0, K_SMALL = 1, K_BIG = 2 };
+
+// A point record: coordinates and index (idx < 0: none).
+struct Cand {
+    float x, y;
+    int idx, pad;
+};
+
+// One point set of the batch.
+struct Inst {
+    long long off, n;
+    long long tile0;   // first tile of this set in the grid-wide tiling (big sets)
+    int kind, K;       // kind, initial polygon size (0: no segments)
+    int tiles;         // tiles of this set
+    int level0;        // first level-0 node
+    unsigned done;     // tiles of the extreme-point pass finished (atomic)
+    int pad;
+    Cand poly[4];      // initial polygon, CCW, starting at the lexicographic minimum
+    int chCount[4];    // points of each initial segment (initial split result)
+    Cand chC[4];       // farthest point of each initial segment
+};
+
+// A segment of the grid-wide rounds: its chord h->e, its points
+// [pstart, pstart + count) of live buffer `buf`, and its farthest point c.
+struct Node {
+    Cand h, e, c;
+    int count, kind;
+    long long pstart;
+    int buf, inst, level, child;  // child: index of the first of its two children (K_BIG)
+    int chCount[2];               // points of the two children (written by the round)
+    Cand chC[2];                  // farthest points of the two children
+    int inner, vc;                // inner vertices (K_SMALL), vertices of the subtree
+    long long off;                // output offset of the subtree within its set
+};
+
+// Decoupled look-back payload of one tile: per slot, the number of points and
+// the farthest point carried for the tile's last (open) parent.
+struct Carry {
+    unsigned cnt[4];
+    Cand best[4];
+};
+
+// Extreme points of a tile: lexicographic min/max of (x, y) and of (y, x).
+struct Ext {
+    Cand a, b, bot, top;
+    int nonfinite, pad[3];
+};
+
+struct Ctl {
+    unsigned err;
+    unsigned bar;        // grid barrier arrivals (monotonic within a launch)
+    unsigned done;       // CTAs finished with a phase (monotonic within a launch)
+    int nBig, nSmallInst;
+    int pad0;
+    long long bigTiles;  // tiles over all big sets
+    int S;               // big segments of the current round
+    int cur;             // bigList buffer of the current round
+    long long L;         // points of the current round
+    long long tiles;     // tiles of the current round
+    int nLevels, nNodes;
+    int levelBase[MAX_LEVELS + 2];
+    int nSmall;          // small-segment queue length
+    unsigned finTicket;
+    int rounds;          // grid-wide rounds run after the initial split
+    int gens;            // generations run (max over sets)
+    long long live[MAX_GEN];
+    unsigned long long exactOrient, exactCmp;
+};
+
+struct Params {
+    const float2 *pts;
+    const long long *offsets;  // nullptr: one set of nSingle points
+    long long nSingle;
+    int numSets;
+    int mode;                  // 0 = quadrilateral, 1 = chord
+    long long ncap;            // plan capacity in points
+    int *outIdx;
+    int *outCounts;
+    float2 *xy[2];             // live points, 2 * ncap each
+    int *id[2];
+    int *vscratch;             // inner vertices of small segments, 2 * ncap
+    unsigned *tstatus;         // look-back status per tile
+    Carry *tagg, *tinc;        // look-back aggregates / inclusive prefixes
+    Ext *text;                 // extreme-point partials per tile
+    long long maxTiles;
+    Inst *inst;
+    int *bigInst, *smallInst;
+    long long *bigTilePrefix;  // exclusive prefix of tiles over big sets (nBig + 1)
+    Node *nodes;
+    int maxNodes;
+    int *bigList[2];
+    long long *vstart[2];      // exclusive prefix of big-segment sizes (S + 1)
+    int maxBig;
+    int *smallQ;
+    Ctl *ctl;
+    int cut;                   // small-segment cutover
+};
+
+// ---------------------------------------------------------------------------
+// Memory-ordering helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(volatile const unsigned *)p; }
+
+__device__ __forceinline__ Cand ldcg_cand(const Cand *p) {
+    int4 v = __ldcg(reinterpret_cast<const int4 *>(p));
+    Cand c;
+    c.x = __int_as_float(v.x);
+    c.y = __int_as_float(v.y);
+    c.idx = v.z;
+    c.pad = v.w;
+    return c;
+}
+__device__ __forceinline__ void stcg_cand(Cand *p, const Cand &c) {
+    __stcg(reinterpret_cast<int4 *>(p), make_int4(__float_as_int(c.x), __float_as_int(c.y), c.idx, c.pad));
+}
+
+__device__ __forceinline__ Cand no_cand() {
+    Cand c;
+    c.x = 0.f;
+    c.y = 0.f;
+    c.idx = -1;
+    c.pad = 0;
+    return c;
+}
+__device__ __forceinline__ Cand mk_cand(float x, float y, int idx) {
+    Cand c;
+    c.x = x;
+    c.y = y;
+    c.idx = idx;
+    c.pad = 0;
+    return c;
+}
+
+__device__ __forceinline__ void set_err(Ctl *ctl, unsigned bits) { atomicOr(&ctl->err, bits); }
+
+// Grid-wide barrier for a cooperative launch.  Every CTA increments `bar`
+// once per barrier; phase counts barriers passed by this CTA.  The wait is
+// bounded: on timeout (or when another CTA reported an error) the error bit is
+// set and false is returned so the kernel can leave.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        phase++;
+        const unsigned target = phase * gridDim.x;
+        __threadfence();
+        atomicAdd(&ctl->bar, 1u);
+        unsigned it = 0;
+        int ok = 1;
+        while (ld_acquire(&ctl->bar) < target) {
+            if (ld_volatile(&ctl->err) != 0u) {
+                ok = 0;
+                break;
+            }
+            if (++it > SPIN_LIMIT) {
+                set_err(ctl, E_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        if (ld_volatile(&ctl->err) != 0u) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide scans (exclusive), NTHREADS threads, scratch of NTHREADS/32 + 1 entries.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+template <typename T, int NTHREADS>
+__device__ __forceinline__ T block_excl_scan(T v, T *scratch, T &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = NTHREADS / 32;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) scratch[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < NW ? scratch[lane] : T(0);
+        T si = warp_incl_scan(s);
+        if (lane < NW) scratch[lane] = si - s;
+        if (lane == NW - 1) scratch[NW] = si;
+    }
+    __syncthreads();
+    T r = scratch[w] + inc - v;
+    total = scratch[NW];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Orderable 32-bit key of a float: unsigned comparison matches float order.
+__device__ __forceinline__ unsigned fkey(float f) {
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ unsigned pkey(float f) { return fkey(f); }
+__device__ __forceinline__ unsigned pkey(double d) { return fkey(__double2float_rd(d)); }
+
+// Host launchers (defined in the .cu files).
+cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
+int rounds_max_ctas_per_sm(int prec);
+cudaError_t launch_finish(const Params &p, int prec, int grid, cudaStream_t s);
+int finish_smem_bytes();
+cudaError_t launch_emit(const Params &p, cudaStream_t s);
+cudaError_t launch_copy(const Params &p, int grid, cudaStream_t s);
+cudaError_t launch_check_orient(const float *tri, long long n, int prec, int *sign, int *cert, cudaStream_t s);
+cudaError_t launch_check_dist(const float *quads, long long n, int *sign, cudaStream_t s);
+
+}  // namespace qh

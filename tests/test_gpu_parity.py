@@ -1,0 +1,166 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Index lists must match bit for bit: the hull is unique under the output rules,
+so no tolerance applies.  Per-generation live counts must match the oracle's
+generation-synchronous QuickHull exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pins
+import synth
+from exact import brute_hull, check_hull_invariants
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def plans(qh):
+    ps = {}
+    for mode in ("quad", "chord"):
+        for prec in ("f32", "f64"):
+            ps[(mode, prec)] = qh.Plan(2_000_000, 1, mode=qh.MODE_QUAD if mode == "quad" else qh.MODE_CHORD,
+                                       prec=qh.PREC_F32 if prec == "f32" else qh.PREC_F64)
+    yield ps
+    for p in ps.values():
+        p.close()
+
+
+def _hull(qh, plan, pts):
+    return qh.hull2d(_dev(pts), plan).cpu().numpy()
+
+
+def test_device_predicates(qh):
+    import torch
+    from test_abi import _triples
+    from exact import orient
+
+    tri = _triples(seed=3)
+    want = np.array([orient(t[0:2], t[2:4], t[4:6]) for t in tri])
+    for prec in (0, 1):
+        s, c = qh.check_orient_device(torch.from_numpy(tri).cuda(), prec)
+        assert np.array_equal(s.cpu().numpy(), want)
+        hs, hc = qh.check_orient_host(tri, prec)
+        assert np.array_equal(c.cpu().numpy(), hc) or prec == 0  # host emulates directed rounding conservatively
+
+
+def test_golden_and_small(qh, plans):
+    cases = [pins.load_golden(p)[0] for p in pins.golden_cases()] + list(pins.small_random_sets(seed=9, count=120))
+    for (mode, prec), plan in plans.items():
+        for p in cases:
+            want = brute_hull(p)
+            got = _hull(qh, plan, p)
+            assert got.tolist() == want, (mode, prec, p.tolist())
+
+
+def test_empty_and_degenerate(qh, plans):
+    plan = plans[("quad", "f32")]
+    assert _hull(qh, plan, np.zeros((0, 2))).tolist() == []
+    assert _hull(qh, plan, np.full((10, 2), 3.0)).tolist() == [0]
+    big_same = np.full((300_000, 2), -1.5, dtype=np.float32)
+    assert _hull(qh, plan, big_same).tolist() == [0]
+    t = np.linspace(-1, 1, 100_001).astype(np.float32)
+    line = np.stack([t, np.float32(0.5) * t], 1)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(len(line))
+    got = _hull(qh, plan, line[perm])
+    assert got.tolist() == oracle.hull2d(line[perm]).tolist()
+    assert len(got) == 2
+
+
+def test_nonfinite_rejected(qh, plans):
+    plan = plans[("quad", "f32")]
+    for n in (50, 100_000):
+        p = synth.disk(n)
+        p[n // 3, 1] = np.nan
+        with pytest.raises(qh.QhError) as e:
+            _hull(qh, plan, p)
+        assert e.value.status == 2
+        p[n // 3, 1] = np.inf
+        with pytest.raises(qh.QhError):
+            _hull(qh, plan, p)
+
+
+@pytest.mark.parametrize("name", ["square", "disk", "circle", "degenerate"])
+@pytest.mark.parametrize("n", [4096, 4097, 6144, 10_001, 150_000])
+def test_workloads_reduced(qh, plans, name, n):
+    p = synth.make(name, n, seed=n)
+    want = oracle.hull2d(p)
+    for key, plan in plans.items():
+        got = _hull(qh, plan, p)
+        assert np.array_equal(got, want), (key, len(got), len(want))
+
+
+@pytest.mark.parametrize("name", ["square", "disk", "circle", "degenerate"])
+@pytest.mark.parametrize("mode", ["quad", "chord"])
+def test_live_counts_match_oracle(qh, plans, name, mode):
+    p = synth.make(name, 300_000, seed=2)
+    plan = plans[(mode, "f32")]
+    got = _hull(qh, plan, p)
+    st = plan.stats()
+    want_hull, want_live = oracle.quickhull(p, mode)
+    assert np.array_equal(got, want_hull)
+    assert st["device_status"] == 0
+    assert st["generations"] == len(want_live)
+    assert st["live"] == want_live.tolist()
+
+
+def test_metamorphic_gpu(qh, plans):
+    plan = plans[("quad", "f32")]
+    p = synth.degenerate(400_000, grid=256)
+    h = _hull(qh, plan, p)
+    assert np.array_equal(_hull(qh, plan, p * np.float32(2.0 ** -20)), h)
+    perm = np.random.default_rng(1).permutation(len(p))
+    hp = _hull(qh, plan, p[perm])
+    assert np.array_equal(p[perm][hp], p[h])
+
+
+def test_batched_matches_per_set(qh):
+    import torch
+
+    p, off = synth.batched(300, seed=4, min_size=1, max_size=40_000)
+    plan = qh.Plan(len(p), 300)
+    out, counts = qh.hull2d_batched(_dev(p), torch.from_numpy(off).cuda(), plan)
+    out = out.cpu().numpy()
+    counts = counts.cpu().numpy()
+    want_out, want_counts = oracle.hull2d_batched(p, off)
+    assert np.array_equal(counts, want_counts)
+    for s in range(len(counts)):
+        a = int(off[s])
+        assert np.array_equal(out[a:a + counts[s]], want_out[a:a + counts[s]]), s
+    plan.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["disk", "circle", "degenerate"])
+def test_full_size(qh, name):
+    p = synth.make(name)
+    plan = qh.Plan(len(p), 1)
+    got = _hull(qh, plan, p)
+    want = oracle.hull2d(p)
+    assert np.array_equal(got, want)
+    check_hull_invariants(p[:200_000], oracle.hull2d(p[:200_000]))
+    plan.close()
+
+
+@pytest.mark.slow
+def test_full_batched(qh):
+    import torch
+
+    p, off = synth.batched()
+    plan = qh.Plan(len(p), len(off) - 1)
+    out, counts = qh.hull2d_batched(_dev(p), torch.from_numpy(off).cuda(), plan)
+    want_out, want_counts = oracle.hull2d_batched(p, off)
+    assert np.array_equal(counts.cpu().numpy(), want_counts)
+    out = out.cpu().numpy()
+    for s in range(len(want_counts)):
+        a = int(off[s])
+        assert np.array_equal(out[a:a + want_counts[s]], want_out[a:a + want_counts[s]]), s
+    plan.close()
