@@ -71,6 +71,10 @@ typedef struct {
     int64_t exact_orient;       /* orientation tests decided by the exact fallback */
     int64_t exact_compare;      /* farthest-point comparisons decided by the exact fallback */
     float phase_ms[5];          /* with timing on: grid rounds, finisher, emit, copy, total */
+    float grid_phase_us[16];    /* inside the grid-wide kernel: set prep, extreme points, initial
+                                   split, then grid-wide rounds 1.. (device clock) */
+    uint64_t section_cycles[16];/* per-tile section cycle sums of CTA thread 0; zero unless the
+                                   library was built with -DQH_PROFILE */
 } qh_stats;
 
 /*

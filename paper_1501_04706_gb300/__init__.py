@@ -45,7 +45,8 @@ class _Stats(ctypes.Structure):
                 ("generations", ctypes.c_int32), ("small_problems", ctypes.c_int32),
                 ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32),
                 ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
-                ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5)]
+                ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5),
+                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 16)]
 
 
 _lib = None
@@ -131,7 +132,9 @@ class Plan:
         return {"device_status": s.device_status, "global_rounds": s.global_rounds, "generations": g,
                 "small_problems": s.small_problems, "nodes": s.nodes, "big_sets": s.big_sets,
                 "live": [int(v) for v in s.live[: min(g, MAX_GEN)]], "exact_orient": int(s.exact_orient),
-                "exact_compare": int(s.exact_compare), "phase_ms": [float(v) for v in s.phase_ms]}
+                "exact_compare": int(s.exact_compare), "phase_ms": [float(v) for v in s.phase_ms],
+                "grid_phase_us": [float(v) for v in s.grid_phase_us if v > 0],
+                "section_cycles": [int(v) for v in s.section_cycles]}
 
 
 def _points_tensor(points):

@@ -38,16 +38,23 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile (if sources changed) and return the path of libqh.so."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out_path: str | None = None) -> str:
+    """Compile (if sources changed) and return the path of libqh.so.
+
+    ``extra`` adds nvcc flags; with ``out_path`` the library (and its objects)
+    go to another file, e.g. for a build with -DQH_PROFILE section counters.
+    """
+    lib_path = out_path or LIB_PATH
+    if out_path is None and not force and not _stale():
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
+    tag = "" if out_path is None else "_" + os.path.splitext(os.path.basename(out_path))[0]
     nvcc = _nvcc()
     extra = list(extra or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + tag + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra]
         if verbose:
             cmd += ["-Xptxas", "-v"]
@@ -67,8 +74,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

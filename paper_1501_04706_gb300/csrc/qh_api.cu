@@ -25,8 +25,7 @@ struct qh_plan_s {
     float2 *xy[2] = {nullptr, nullptr};
     int *id[2] = {nullptr, nullptr};
     int *vscratch = nullptr;
-    unsigned *tstatus = nullptr;
-    Carry *tagg = nullptr, *tinc = nullptr;
+    Cand *tbest = nullptr;
     Ext *text = nullptr;
     long long maxTiles = 0;
     Inst *inst = nullptr;
@@ -72,9 +71,7 @@ void plan_free(qh_plan p) {
     cudaFree(p->id[0]);
     cudaFree(p->id[1]);
     cudaFree(p->vscratch);
-    cudaFree(p->tstatus);
-    cudaFree(p->tagg);
-    cudaFree(p->tinc);
+    cudaFree(p->tbest);
     cudaFree(p->text);
     cudaFree(p->inst);
     cudaFree(p->bigInst);
@@ -110,9 +107,7 @@ qh_status plan_alloc(qh_plan p) {
     QH_ALLOC(p->id[1], 2 * N);
     QH_ALLOC(p->vscratch, 2 * N);
     p->maxTiles = N / TILE + p->maxSets + 16;
-    QH_ALLOC(p->tstatus, p->maxTiles);
-    QH_ALLOC(p->tagg, p->maxTiles);
-    QH_ALLOC(p->tinc, p->maxTiles);
+    QH_ALLOC(p->tbest, 4 * p->maxTiles);
     QH_ALLOC(p->text, p->maxTiles);
     QH_ALLOC(p->inst, p->maxSets);
     QH_ALLOC(p->bigInst, p->maxSets + 1);
@@ -162,9 +157,7 @@ Params make_params(qh_plan pl, const float *points, const long long *offsets, lo
         p.vstart[b] = pl->vstart[b];
     }
     p.vscratch = pl->vscratch;
-    p.tstatus = pl->tstatus;
-    p.tagg = pl->tagg;
-    p.tinc = pl->tinc;
+    p.tbest = pl->tbest;
     p.text = pl->text;
     p.maxTiles = pl->maxTiles;
     p.inst = pl->inst;
@@ -188,7 +181,6 @@ qh_status run(qh_plan pl, const float *points, const long long *offsets, long lo
     const int prec = (pl->flags & QH_PREC_F64) ? 1 : 0;
     Params p = make_params(pl, points, offsets, nSingle, numSets, outIdx, outCounts);
     cudaError_t e = cudaMemsetAsync(pl->ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pl->tstatus, 0, sizeof(unsigned) * (size_t)pl->maxTiles, s);
     if (e != cudaSuccess) return cuda_status(e);
     const bool tm = pl->timing != 0;
     if (tm) cudaEventRecord(pl->ev[0], s);
@@ -395,8 +387,14 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
         if (c.live[g] > 0) last = g;
     }
     out->generations = last < 0 ? 1 : last + 2;
+    for (int k = 0; k < 16; k++) out->section_cycles[k] = c.prof[k];
     out->exact_orient = (int64_t)c.exactOrient;
     out->exact_compare = (int64_t)c.exactCmp;
+    for (int k = 0; k < 16; k++) {
+        const int hi = k + 1;
+        if (hi >= MAX_LEVELS + 4 || c.tphase[hi] == 0ull || c.tphase[k] == 0ull) break;
+        out->grid_phase_us[k] = (float)((double)(c.tphase[hi] - c.tphase[k]) * 1e-3);
+    }
     if (plan->evRecorded) {
         for (int k = 0; k < 4; k++) cudaEventElapsedTime(&out->phase_ms[k], plan->ev[k], plan->ev[k + 1]);
         cudaEventElapsedTime(&out->phase_ms[4], plan->ev[0], plan->ev[4]);

@@ -34,6 +34,7 @@ struct FinSmem {
     unsigned short best[2 * FM];
     unsigned short newId[2 * FM];
     int scan[FIN_NT / 32 + 1];
+    long long scan64[FIN_NT / 32 + 1];
     int ticket, cLocal, nOrd, S, K, degenerate, nonfinite;
     long long liveCount;
     unsigned short poly[4];
@@ -105,42 +106,67 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
     }
     for (int j = threadIdx.x; j < (initial ? s.K : S); j += FIN_NT) s.cnt2[j] = 0u;
     __syncthreads();
-    // pass 1: classify
-    for (int k = threadIdx.x; k < m; k += FIN_NT) {
-        const unsigned short j = s.seg[k];
-        if (j == NONE16) continue;
-        const float2 q = s.pxy[k];
-        P lo = P(0), hi = P(0);
+    // pass 1: classify.  The per-child counters are updated once per group of
+    // lanes that share a child (same-address shared atomics would serialise).
+    for (int k0 = 0; k0 < m; k0 += FIN_NT) {
+        const int k = k0 + threadIdx.x;
         int child = -1;
-        if (initial) {
-            for (int c = 0; c < s.K; c++) {
-                int u, v;
-                child_chord(s, ord, nOrd, true, c, u, v);
-                if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
-                    child = c;
-                    break;
+        unsigned key = 0u;
+        if (k < m) {
+            const unsigned short j = s.seg[k];
+            if (j != NONE16) {
+                const float2 q = s.pxy[k];
+                P lo = P(0), hi = P(0);
+                if (initial) {
+                    for (int c = 0; c < s.K; c++) {
+                        int u, v;
+                        child_chord(s, ord, nOrd, true, c, u, v);
+                        if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
+                            child = c;
+                            break;
+                        }
+                    }
+                } else {
+                    int u, v;
+                    child_chord(s, ord, nOrd, false, 2 * j, u, v);
+                    if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
+                        child = 2 * j;
+                    } else {
+                        child_chord(s, ord, nOrd, false, 2 * j + 1, u, v);
+                        if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) child = 2 * j + 1;
+                    }
                 }
-            }
-        } else {
-            int u, v;
-            child_chord(s, ord, nOrd, false, 2 * j, u, v);
-            if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) {
-                child = 2 * j;
-            } else {
-                child_chord(s, ord, nOrd, false, 2 * j + 1, u, v);
-                if (fin_right_of(s, u, v, q.x, q.y, lo, hi, exact_o)) child = 2 * j + 1;
+                s.seg[k] = child < 0 ? NONE16 : (unsigned short)child;
+                key = max(pkey(lo), 1u);
             }
         }
-        if (child < 0) {
-            s.seg[k] = NONE16;
-            continue;
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        const unsigned grp = __match_any_sync(full, child);
+        const bool leader = child >= 0 && lane == __ffs(grp) - 1;
+        unsigned leaders = __ballot_sync(full, leader);
+        if (__popc(leaders) <= 4) {
+            while (leaders) {
+                const int l = __ffs(leaders) - 1;
+                const int c = __shfl_sync(full, child, l);
+                const unsigned mx = __reduce_max_sync(full, child == c ? key : 0u);
+                if (lane == l) {
+                    const unsigned cnt = __popc(grp);
+                    if (initial)
+                        atomicAdd(&s.cnt2[c], cnt);
+                    else
+                        atomicAdd(&s.cnt2[c >> 1], (c & 1) ? cnt << 16 : cnt);
+                    atomicMax(&s.maxLo[c], mx);
+                }
+                leaders &= leaders - 1;
+            }
+        } else if (child >= 0) {
+            if (initial)
+                atomicAdd(&s.cnt2[child], 1u);
+            else
+                atomicAdd(&s.cnt2[child >> 1], (child & 1) ? 0x10000u : 1u);
+            atomicMax(&s.maxLo[child], key);
         }
-        s.seg[k] = (unsigned short)child;
-        if (initial)
-            atomicAdd(&s.cnt2[child], 1u);
-        else
-            atomicAdd(&s.cnt2[child >> 1], (child & 1) ? 0x10000u : 1u);
-        atomicMax(&s.maxLo[child], max(pkey(lo), 1u));
     }
     __syncthreads();
     // pass 2: exact farthest point among the candidates of each child
@@ -191,12 +217,12 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
             const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
             s.newId[c] = cnt > 0u ? (unsigned short)(x++) : NONE16;
         }
+        long long ptot;
+        block_excl_scan<long long, FIN_NT>(pts, reinterpret_cast<long long *>(s.scan64), ptot);
         if (threadIdx.x == 0) {
             s.S = tot;
-            s.liveCount = 0;
+            s.liveCount = ptot;
         }
-        __syncthreads();
-        if (pts) atomicAdd((unsigned long long *)&s.liveCount, (unsigned long long)pts);
     }
     __syncthreads();
     // new CCW list of heads

@@ -14,7 +14,14 @@ namespace qh {
 // ---------------------------------------------------------------------------
 // Tunables
 // ---------------------------------------------------------------------------
-constexpr int NT = 512;            // threads per CTA of the grid-wide kernel
+#ifndef QH_NT
+#define QH_NT 256
+#endif
+#ifndef QH_MINB
+#define QH_MINB 4
+#endif
+constexpr int NT = QH_NT;          // threads per CTA of the grid-wide kernel
+constexpr int MINB = QH_MINB;      // CTAs per SM the grid-wide kernel is built for
 constexpr int NWARP = NT / 32;
 constexpr int IPT = 4;             // points per thread per tile (warp-striped rows)
 constexpr int TILE = NT * IPT;     // points per tile
@@ -32,8 +39,9 @@ enum : int { I_EMPTY = 0, I_SMALL = 1, I_BIG = 2, I_DEGEN = 3, I_NONFINITE = 4 }
 // segment (node) kinds
 enum : int { K_LEAF = 0, K_SMALL = 1, K_BIG = 2 };
 
-// A point record: coordinates and index (idx < 0: none).
-struct Cand {
+// A point record: coordinates and index (idx < 0: none).  16-byte aligned:
+// records move through global memory as single 16-byte accesses.
+struct __align__(16) Cand {
     float x, y;
     int idx, pad;
 };
@@ -46,9 +54,11 @@ struct Inst {
     int tiles;         // tiles of this set
     int level0;        // first level-0 node
     unsigned done;     // tiles of the extreme-point pass finished (atomic)
-    int pad;
+    unsigned done0;    // tiles of the initial split finished (atomic)
     Cand poly[4];      // initial polygon, CCW, starting at the lexicographic minimum
-    int chCount[4];    // points of each initial segment (initial split result)
+    int iB, hasBox;    // index of the rightmost vertex B in poly; inner box valid
+    float box[4];      // x0, x1, y0, y1 of an axis-aligned box inside the closed polygon
+    int chCount[4];    // points of each initial segment: output cursors during the split (atomic)
     Cand chC[4];       // farthest point of each initial segment
 };
 
@@ -59,17 +69,12 @@ struct Node {
     int count, kind;
     long long pstart;
     int buf, inst, level, child;  // child: index of the first of its two children (K_BIG)
-    int chCount[2];               // points of the two children (written by the round)
+    int chCount[2];               // points of the two children: output cursors during the round (atomic)
     Cand chC[2];                  // farthest points of the two children
     int inner, vc;                // inner vertices (K_SMALL), vertices of the subtree
     long long off;                // output offset of the subtree within its set
-};
-
-// Decoupled look-back payload of one tile: per slot, the number of points and
-// the farthest point carried for the tile's last (open) parent.
-struct Carry {
-    unsigned cnt[4];
-    Cand best[4];
+    unsigned tdone;               // tiles of the round that finished with this segment (atomic)
+    int pad2[3];
 };
 
 // Extreme points of a tile: lexicographic min/max of (x, y) and of (y, x).
@@ -97,6 +102,8 @@ struct Ctl {
     int gens;            // generations run (max over sets)
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;
+    unsigned long long tphase[MAX_LEVELS + 4];  // %globaltimer at the kernel start and after each grid barrier
+    unsigned long long prof[16];                // section cycle counters (profiling builds only)
 };
 
 struct Params {
@@ -111,8 +118,7 @@ struct Params {
     float2 *xy[2];             // live points, 2 * ncap each
     int *id[2];
     int *vscratch;             // inner vertices of small segments, 2 * ncap
-    unsigned *tstatus;         // look-back status per tile
-    Carry *tagg, *tinc;        // look-back aggregates / inclusive prefixes
+    Cand *tbest;               // per tile and slot: the tile's exact farthest point (4 per tile)
     Ext *text;                 // extreme-point partials per tile
     long long maxTiles;
     Inst *inst;
@@ -172,6 +178,44 @@ __device__ __forceinline__ Cand mk_cand(float x, float y, int idx) {
 }
 
 __device__ __forceinline__ void set_err(Ctl *ctl, unsigned bits) { atomicOr(&ctl->err, bits); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Section cycle counters of thread 0, compiled in with -DQH_PROFILE.
+#ifdef QH_PROFILE
+#define QH_PROF_DECL unsigned long long qh_prof_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}; long long qh_prof_t = clock64()
+#define QH_PROF(k)                                         \
+    do {                                                   \
+        if (threadIdx.x == 0) {                            \
+            const long long qh_now = clock64();            \
+            qh_prof_acc[k] += (unsigned long long)(qh_now - qh_prof_t); \
+            qh_prof_t = qh_now;                            \
+        }                                                  \
+    } while (0)
+#define QH_PROF_FLUSH(ctl)                                                    \
+    do {                                                                      \
+        if (threadIdx.x == 0)                                                 \
+            for (int qh_k = 0; qh_k < 8; qh_k++) atomicAdd(&(ctl)->prof[qh_k], qh_prof_acc[qh_k]); \
+    } while (0)
+#define QH_PROF_FLUSH_AT(ctl, base)                                           \
+    do {                                                                      \
+        if (threadIdx.x == 0)                                                 \
+            for (int qh_k = 0; qh_k < 8; qh_k++) atomicAdd(&(ctl)->prof[(base) + qh_k], qh_prof_acc[qh_k]); \
+    } while (0)
+#else
+#define QH_PROF_DECL
+#define QH_PROF(k)
+#define QH_PROF_FLUSH(ctl)
+#define QH_PROF_FLUSH_AT(ctl, base)
+#endif
+
+// Phase timestamp, written by CTA 0 after a grid barrier.
+__device__ __forceinline__ void stamp(Ctl *ctl, int k) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && k < MAX_LEVELS + 4) ctl->tphase[k] = global_ns();
+}
 
 // Grid-wide barrier for a cooperative launch.  Every CTA increments `bar`
 // once per barrier; phase counts barriers passed by this CTA.  The wait is

@@ -32,8 +32,11 @@
 
 #if defined(__CUDACC__)
 #define QH_HD __host__ __device__ __forceinline__
+// The exact fallback is rare: kept out of line so its registers do not burden the fast path.
+#define QH_HD_COLD static __host__ __device__ __noinline__
 #else
 #define QH_HD inline
+#define QH_HD_COLD static inline
 #endif
 
 namespace qh {
@@ -193,14 +196,14 @@ QH_HD int expansion_sign(const double *t, int n) {
 QH_HD double xp(float a, float b) { return rmul(double(a), double(b)); }
 
 // orient(a,b,c) = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx, exactly.
-QH_HD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
+QH_HD_COLD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
     double t[6] = {xp(bx, cy), -xp(bx, ay), -xp(ax, cy), -xp(by, cx), xp(by, ax), xp(ay, cx)};
     return expansion_sign(t, 6);
 }
 
 // sign(dist(p) - dist(q)) for the chord u->v, dist(x) = -orient(u, v, x):
 //   -(vx-ux)(py-qy) + (vy-uy)(px-qx), expanded into eight exact products.
-QH_HD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, float py, float qx, float qy) {
+QH_HD_COLD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, float py, float qx, float qy) {
     double t[8] = {-xp(vx, py), xp(vx, qy), xp(ux, py), -xp(ux, qy),
                    xp(vy, px), -xp(vy, qx), -xp(uy, px), xp(uy, qx)};
     return expansion_sign(t, 8);

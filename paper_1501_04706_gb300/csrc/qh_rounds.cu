@@ -4,8 +4,9 @@
 //   prep       CTA 0 classifies the sets: empty, small (<= FIN_MAX points, left
 //              to the block finisher) or big (tiled here).
 //   extremes   per big set, the four extreme points of Sec. 4.2 (lexicographic
-//              min/max of (x, y) and of (y, x), ties to the lower index), as a
-//              tile reduction whose last tile merges the set's partials.
+//              min/max of (x, y) and of (y, x), ties to the lower index).  Each
+//              CTA streams a contiguous chunk of tiles and keeps running
+//              extremes; the CTA that completes a set merges its partials.
 //   round 0    the initial split (Sec. 4.2-4.3): each point joins the first
 //              edge of the initial polygon it lies strictly right of (the
 //              quadrilateral A->Bot->B->Top, or the chord A->B / B->A), and is
@@ -17,39 +18,172 @@
 //              and find each child's farthest point (Sec. 4.4.1) in the same
 //              pass; then the last CTA builds the next level of segments.
 //
-// Compaction is a single pass with a decoupled look-back over tiles of TILE
-// points.  Segments are contiguous ranges of a live buffer; a child never
-// leaves its parent's range: the first child grows upward from the parent's
-// start, the second downward from its end, so the positions only need the
-// parent-local (segmented) counts that the look-back carries, together with
-// the farthest point seen so far (the segmented argmax).  Segments with at
-// most `cut` points (cut >= TILE) leave the grid-wide rounds for the block
-// finisher, so a tile of a round spans at most two segments.
+// Memory pipeline: every CTA owns a ring of NS shared-memory stages filled by
+// TMA bulk copies (cp.async.bulk + mbarrier).  Thread 0 resolves the segment
+// descriptors of tile k + NS and starts its copies while the CTA works on tile
+// k, so HBM latency and descriptor lookups overlap the per-tile work.
+//
+// Compaction is a single pass.  Segments are contiguous ranges of a live
+// buffer and a child never leaves its parent's range: the first child grows
+// upward from the parent's start, the second downward from its end.  Every
+// tile reserves its output range in each child with one atomic add on the
+// child's cursor, so no tile ever waits for another (a tile-ordered scan would
+// chain the ~600 tiles a persistent grid has in flight; the order of points
+// inside a segment is irrelevant to the method).  The farthest point of each
+// child is exact: each tile stores its own exact best per child, and the last
+// tile of a parent (per-parent tile counter) merges the parent's tile bests.
+// Segments with at most `cut` points (cut >= TILE) leave the grid-wide rounds
+// for the block finisher, so a tile of a round spans at most two segments.
 #include "qh_internal.cuh"
 
 namespace qh {
 
+constexpr int NS = 3;          // pipeline stages per CTA
+constexpr int DB = 16;         // tile descriptors resolved per batch (one thread per tile)
+constexpr int CAND_CAP = 128;  // farthest-point candidates kept per tile before the fallback
+
+// Items of one segment inside a tile: physical range [q0, q0 + c) of the
+// source buffer, first tile-local item vofs; [a0, a1) / [b0, b1) are the
+// 16-byte aligned interiors copied by TMA to stage offsets sx / si (the
+// ragged ends, at most one point on each side, are read directly).
+struct PartGeo {
+    long long q0, a0, a1, b0, b1;
+    int c, vofs, sx, si;
+};
+
+struct TileRec {
+    long long t;
+    int np, nItems, valid, inst;
+    unsigned bytes;  // TMA bytes of the tile
+    int srcBuf;      // live buffer read by a round tile
+    // round 0 / extremes: the set
+    long long lt, setOff, setN, tile0;
+    int tiles, K, iB, hasBox;
+    float box[4];
+    Cand poly[4];
+    // rounds: the (at most two) parent segments
+    int node[2], count[2];
+    long long vstart[2], pstart[2];
+    Cand nh[2], ne[2], nc[2];
+    PartGeo g[2];
+};
+
+struct StageBuf {
+    float2 xy[TILE];
+    int id[TILE];
+};
+
 template <typename P> struct RoundSmem {
-    // tile descriptors
-    Edge<P> edge[4];
-    float vend[4][2];  // end point of each slot's chord (for the exact fallback)
-    long long pstart[2], vstart[2];
-    int count[2], node[2];
-    int nparts, inst, kflag;
-    long long lt;
-    // ranks
+    unsigned long long mbar[NS];
+    TileRec desc[2][DB];  // descriptors of the CTA's tiles, double-buffered by batch
+    // tile working set
+    Edge<P> edge[5];   // per slot; edge[4]: the chord A->B of the initial split
+    float vend[5][2];
+    int kflag;
     unsigned long long warpTot[IPT * NWARP];
     unsigned long long tileTot;
-    // farthest point
     unsigned maxLo[4];
     int ncand;
     Cand best[4];
-    Carry carry;
+    Cand fin[4];
+    int base[4];   // this tile's first output rank in each slot's child
+    int fflag[2];  // this tile is the last of part A / part B's parent
     long long scanTmp[NWARP + 1];
     Ext wext[NWARP];
-    Cand cand[TILE];
-    unsigned char cslot[TILE];
+    Cand wbest[NWARP][4];
+    Cand cand[CAND_CAP];
+    unsigned char cslot[CAND_CAP];
+    alignas(128) StageBuf stage[NS];
 };
+
+// --------------------------------------------------------------------------
+// TMA / mbarrier helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// 1-D bulk copy global -> shared, completing on mbarrier b (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Bounded wait for stage s; false (error bit set) when it never completes.
+template <typename P> __device__ __forceinline__ bool pipe_wait(const Params &p, RoundSmem<P> &sm, int s, unsigned par) {
+    unsigned it = 0;
+    while (!mbar_try_wait(&sm.mbar[s], par)) {
+        if (++it > SPIN_LIMIT) {
+            set_err(p.ctl, E_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// xyPhase / idPhase: element offset of the array base from a 16-byte boundary
+// (0/1 float2, 0..3 int), so that the copied interior is 16-byte aligned in memory.
+__device__ __forceinline__ void part_geo(PartGeo &g, long long q0, int c, int vofs, bool withId, int &sx, int &si,
+                                         unsigned &bytes, int xyPhase, int idPhase) {
+    g.q0 = q0;
+    g.c = c;
+    g.vofs = vofs;
+    const long long end = q0 + c;
+    long long a0 = q0 + ((q0 + xyPhase) & 1), a1 = end - ((end + xyPhase) & 1);
+    if (a1 < a0) a1 = a0;
+    g.a0 = a0;
+    g.a1 = a1;
+    g.sx = sx;
+    sx += (int)(a1 - a0);
+    bytes += (unsigned)(a1 - a0) * 8u;
+    if (withId) {
+        long long b0 = q0 + ((4 - ((q0 + idPhase) & 3)) & 3), b1 = end - ((end + idPhase) & 3);
+        if (b1 < b0) b1 = b0;
+        g.b0 = b0;
+        g.b1 = b1;
+        g.si = si;
+        si += (int)(b1 - b0);
+        bytes += (unsigned)(b1 - b0) * 4u;
+    } else {
+        g.b0 = g.b1 = 0;
+        g.si = 0;
+    }
+}
+
+__device__ __forceinline__ int part_of(const TileRec &R, int i) { return (R.np == 2 && i >= R.g[1].vofs) ? 1 : 0; }
+
+__device__ __forceinline__ float2 fetch_xy(const TileRec &R, const StageBuf &S, int i, const float2 *gxy,
+                                           bool readOnly) {
+    const PartGeo &g = R.g[part_of(R, i)];
+    const long long q = g.q0 + (i - g.vofs);
+    if (q >= g.a0 && q < g.a1) return S.xy[g.sx + (int)(q - g.a0)];
+    return readOnly ? __ldg(&gxy[q]) : __ldcg(&gxy[q]);
+}
+__device__ __forceinline__ int fetch_id(const TileRec &R, const StageBuf &S, int i, const int *gid) {
+    const PartGeo &g = R.g[part_of(R, i)];
+    const long long q = g.q0 + (i - g.vofs);
+    if (q >= g.b0 && q < g.b1) return S.id[g.si + (int)(q - g.b0)];
+    return __ldcg(&gid[q]);
+}
 
 // --------------------------------------------------------------------------
 // small helpers
@@ -140,74 +274,6 @@ __device__ __forceinline__ bool last_cta(Ctl *ctl, unsigned &donePhase, int *fla
 }
 
 // --------------------------------------------------------------------------
-// look-back helpers (thread 0 only)
-// --------------------------------------------------------------------------
-__device__ __forceinline__ void publish(const Params &p, long long t, unsigned epoch, unsigned state,
-                                        const Carry &c, int nslot) {
-    Carry *dst = state == 2u ? &p.tinc[t] : &p.tagg[t];
-    for (int s = 0; s < nslot; s++) {
-        __stcg(&dst->cnt[s], c.cnt[s]);
-        stcg_cand(&dst->best[s], c.best[s]);
-    }
-    __threadfence();
-    st_release(&p.tstatus[t], (epoch << 2) | state);
-}
-
-template <typename P>
-__device__ __forceinline__ void carry_merge(Carry &acc, const Carry &x, int nslot, const RoundSmem<P> &sm,
-                                            int &exact_c) {
-    for (int s = 0; s < nslot; s++) {
-        acc.cnt[s] += x.cnt[s];
-        const Edge<P> &e = sm.edge[s];
-        const Cand &a = x.best[s];
-        const Cand &b = acc.best[s];
-        if (a.idx < 0) continue;
-        if (b.idx < 0) {
-            acc.best[s] = a;
-            continue;
-        }
-        DistIv<P> da = dist_interval(orient_approx(e, a.x, a.y));
-        DistIv<P> db = dist_interval(orient_approx(e, b.x, b.y));
-        if (farther(e, sm.vend[s][0], sm.vend[s][1], a.x, a.y, a.idx, da, b.x, b.y, b.idx, db, exact_c))
-            acc.best[s] = a;
-    }
-}
-
-// Exclusive carry of tile t for its first parent: sum of the predecessors'
-// payloads back to (and including) the first inclusive one.
-template <typename P>
-__device__ bool lookback(const Params &p, long long t, unsigned epoch, int nslot, const RoundSmem<P> &sm,
-                         Carry &acc, int &exact_c) {
-    for (int s = 0; s < 4; s++) {
-        acc.cnt[s] = 0u;
-        acc.best[s] = no_cand();
-    }
-    for (long long u = t - 1; u >= 0; u--) {
-        unsigned st, it = 0;
-        for (;;) {
-            st = ld_acquire(&p.tstatus[u]);
-            if ((st >> 2) == epoch && (st & 3u) != 0u) break;
-            if (ld_volatile(&p.ctl->err) != 0u) return false;
-            if (++it > SPIN_LIMIT) {
-                set_err(p.ctl, E_TIMEOUT);
-                return false;
-            }
-            __nanosleep(32);
-        }
-        const Carry *src = (st & 3u) == 2u ? &p.tinc[u] : &p.tagg[u];
-        Carry x;
-        for (int s = 0; s < nslot; s++) {
-            x.cnt[s] = __ldcg(&src->cnt[s]);
-            x.best[s] = ldcg_cand(&src->best[s]);
-        }
-        carry_merge(acc, x, nslot, sm, exact_c);
-        if ((st & 3u) == 2u) return true;
-    }
-    set_err(p.ctl, E_INTERNAL);  // a chain must end at an inclusive tile
-    return false;
-}
-
-// --------------------------------------------------------------------------
 // per-tile ranks and farthest points
 // --------------------------------------------------------------------------
 // slot[k] in {-1, 0..3} for the item of row k; rank[k] receives its exclusive
@@ -257,14 +323,30 @@ __device__ __forceinline__ void tile_ranks(const int (&slot)[IPT], int (&rank)[I
     for (int s = 0; s < 4; s++) tot[s] = (unsigned)((sm.tileTot >> (16 * s)) & 0xffffull);
 }
 
+// Merge candidate b into a for the chord of slot s (exact order).
+template <typename P>
+__device__ __forceinline__ void cand_merge(Cand &a, const Cand &b, int s, const RoundSmem<P> &sm, int &exact_c) {
+    if (b.idx < 0) return;
+    if (a.idx < 0) {
+        a = b;
+        return;
+    }
+    const Edge<P> &e = sm.edge[s];
+    const DistIv<P> da = dist_interval(orient_approx(e, a.x, a.y));
+    const DistIv<P> db = dist_interval(orient_approx(e, b.x, b.y));
+    if (farther(e, sm.vend[s][0], sm.vend[s][1], b.x, b.y, b.idx, db, a.x, a.y, a.idx, da, exact_c)) a = b;
+}
+
 // Farthest point of each slot within the tile, exactly: the largest lower
 // bound per slot, then every item whose upper bound reaches it is a candidate,
-// and thread s picks the best candidate of slot s with the exact order.
+// and thread s picks the best candidate of slot s with the exact order.  When
+// more than CAND_CAP items are candidates (massive exact ties), every thread
+// reduces its own candidates and the warps combine them with the exact order.
 template <typename P>
 __device__ __forceinline__ void tile_farthest(const int (&slot)[IPT], const float (&x)[IPT], const float (&y)[IPT],
                                               const int (&idx)[IPT], const P (&lo)[IPT], const P (&hi)[IPT],
                                               RoundSmem<P> &sm, int &exact_c) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x < 4) sm.maxLo[threadIdx.x] = 0u;
     if (threadIdx.x == 0) sm.ncand = 0;
     __syncthreads();
@@ -273,7 +355,7 @@ __device__ __forceinline__ void tile_farthest(const int (&slot)[IPT], const floa
     for (int k = 0; k < IPT; k++) {
 #pragma unroll
         for (int s = 0; s < 4; s++)
-            if (slot[k] == s) mk[s] = max(mk[s], pkey(lo[k]));
+            if (slot[k] == s) mk[s] = max(mk[s], max(pkey(lo[k]), 1u));
     }
 #pragma unroll
     for (int s = 0; s < 4; s++) {
@@ -281,35 +363,49 @@ __device__ __forceinline__ void tile_farthest(const int (&slot)[IPT], const floa
         if (lane == 0 && v != 0u) atomicMax(&sm.maxLo[s], v);
     }
     __syncthreads();
+    bool cand[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; k++) {
+        cand[k] = false;
         if (slot[k] >= 0) {
-            P thr = (P)fkey_inv(sm.maxLo[slot[k]]);
+            const P thr = (P)fkey_inv(sm.maxLo[slot[k]]);
             if (hi[k] >= thr) {
+                cand[k] = true;
                 int j = atomicAdd(&sm.ncand, 1);
-                sm.cand[j] = mk_cand(x[k], y[k], idx[k]);
-                sm.cslot[j] = (unsigned char)slot[k];
+                if (j < CAND_CAP) {
+                    sm.cand[j] = mk_cand(x[k], y[k], idx[k]);
+                    sm.cslot[j] = (unsigned char)slot[k];
+                }
             }
         }
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
-        const int s = threadIdx.x;
-        const Edge<P> &e = sm.edge[s];
-        Cand b = no_cand();
-        DistIv<P> db;
-        db.lo = db.hi = P(0);
-        const int nc = sm.ncand;
-        for (int j = 0; j < nc; j++) {
-            if (sm.cslot[j] != s) continue;
-            const Cand a = sm.cand[j];
-            DistIv<P> da = dist_interval(orient_approx(e, a.x, a.y));
-            if (farther(e, sm.vend[s][0], sm.vend[s][1], a.x, a.y, a.idx, da, b.x, b.y, b.idx, db, exact_c)) {
-                b = a;
-                db = da;
-            }
+    const int nc = sm.ncand;
+    if (nc <= CAND_CAP) {
+        if (threadIdx.x < 4) {
+            const int s = threadIdx.x;
+            Cand b = no_cand();
+            for (int j = 0; j < nc; j++)
+                if (sm.cslot[j] == s) cand_merge(b, sm.cand[j], s, sm, exact_c);
+            sm.best[s] = b;
         }
-        sm.best[s] = b;
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < 4; s++) {
+            Cand b = no_cand();
+#pragma unroll
+            for (int k = 0; k < IPT; k++)
+                if (cand[k] && slot[k] == s) cand_merge(b, mk_cand(x[k], y[k], idx[k]), s, sm, exact_c);
+            for (int d = 16; d >= 1; d >>= 1) cand_merge(b, shfl_cand(b, lane ^ d), s, sm, exact_c);
+            if (lane == 0) sm.wbest[w][s] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            const int s = threadIdx.x;
+            Cand b = no_cand();
+            for (int j = 0; j < NWARP; j++) cand_merge(b, sm.wbest[j][s], s, sm, exact_c);
+            sm.best[s] = b;
+        }
     }
     __syncthreads();
 }
@@ -331,9 +427,44 @@ __device__ __forceinline__ bool right_of(const Edge<P> &e, float vx, float vy, f
 }
 
 // --------------------------------------------------------------------------
+// per-tile farthest points and their merge per parent
+// --------------------------------------------------------------------------
+// Thread of warp 1: the tile's own farthest points, read by the parent's last tile.
+__device__ __forceinline__ void store_tile_bests(const Params &p, long long t, const Cand (&b)[4]) {
+    for (int s = 0; s < 4; s++) stcg_cand(&p.tbest[4 * t + s], b[s]);
+}
+
+// Exact farthest point of each of the nslot children of a parent whose points
+// span tiles [ta, tb]: merge of the per-tile bests (tile ta reads its slots
+// from slotBase0, the others from 0) with the chords sm.edge[edgeOff ..
+// edgeOff + nslot).  Whole CTA; result in sm.fin.
+template <typename P>
+__device__ __noinline__ void merge_parent_bests(const Params &p, RoundSmem<P> &sm, long long ta, long long tb, int slotBase0,
+                                   int nslot, int edgeOff, int &exact_c) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Cand b[4] = {no_cand(), no_cand(), no_cand(), no_cand()};
+    for (long long u = ta + threadIdx.x; u <= tb; u += NT) {
+        const int base = (u == ta) ? slotBase0 : 0;
+        for (int s = 0; s < nslot; s++)
+            cand_merge(b[s], ldcg_cand(&p.tbest[4 * u + base + s]), edgeOff + s, sm, exact_c);
+    }
+    for (int s = 0; s < nslot; s++) {
+        for (int d = 16; d >= 1; d >>= 1) cand_merge(b[s], shfl_cand(b[s], lane ^ d), edgeOff + s, sm, exact_c);
+        if (lane == 0) sm.wbest[w][s] = b[s];
+    }
+    __syncthreads();
+    if (threadIdx.x < nslot) {
+        Cand r = no_cand();
+        for (int k = 0; k < NWARP; k++) cand_merge(r, sm.wbest[k][threadIdx.x], edgeOff + threadIdx.x, sm, exact_c);
+        sm.fin[threadIdx.x] = r;
+    }
+    __syncthreads();
+}
+
+// --------------------------------------------------------------------------
 // prep: classify sets (CTA 0)
 // --------------------------------------------------------------------------
-template <typename P> __device__ void prep(const Params &p, RoundSmem<P> &sm) {
+template <typename P> __device__ __noinline__ void prep(const Params &p, RoundSmem<P> &sm) {
     long long *scr = sm.scanTmp;
     long long carryBig = 0, carrySmall = 0, carryTiles = 0;
     for (int base = 0; base < p.numSets; base += NT) {
@@ -371,6 +502,8 @@ template <typename P> __device__ void prep(const Params &p, RoundSmem<P> &sm) {
             I.tile0 = carryTiles + xt;
             I.level0 = -1;
             I.done = 0u;
+            I.done0 = 0u;
+            for (int k = 0; k < 4; k++) I.chCount[k] = 0;
             if (kind == I_BIG) {
                 p.bigInst[carryBig + xb] = i;
                 p.bigTilePrefix[carryBig + xb] = carryTiles + xt;
@@ -401,61 +534,245 @@ template <typename P> __device__ void prep(const Params &p, RoundSmem<P> &sm) {
 }
 
 // --------------------------------------------------------------------------
-// extremes (Sec. 4.2)
+// tile descriptors: resolved in batches, one thread per tile, so the lookups
+// (binary searches, segment records) of DB tiles overlap; thread 0 then only
+// copies a descriptor and starts its TMA copies.
 // --------------------------------------------------------------------------
-template <typename P> __device__ void locate_tile(const Params &p, RoundSmem<P> &sm, long long t) {
-    if (threadIdx.x == 0) {
-        const int nBig = __ldcg(&p.ctl->nBig);
-        long long j = upper_bound_ll(p.bigTilePrefix, nBig + 1, t) - 1;
-        sm.inst = __ldcg(&p.bigInst[j]);
-        sm.lt = t - __ldcg(&p.bigTilePrefix[j]);
+__device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool withPoly) {
+    const int nBig = __ldcg(&p.ctl->nBig);
+    const long long j = upper_bound_ll(p.bigTilePrefix, nBig + 1, t) - 1;
+    const int i = __ldcg(&p.bigInst[j]);
+    const Inst *I = &p.inst[i];
+    R.t = t;
+    R.inst = i;
+    R.np = 1;
+    R.valid = 1;
+    R.srcBuf = 0;
+    R.lt = t - __ldcg(&p.bigTilePrefix[j]);
+    R.setOff = __ldcg(&I->off);
+    R.setN = __ldcg(&I->n);
+    R.tile0 = __ldcg(&I->tile0);
+    R.tiles = __ldcg(&I->tiles);
+    R.K = 0;
+    R.iB = 1;
+    R.hasBox = 0;
+    if (withPoly) {
+        R.K = __ldcg(&I->K);
+        R.iB = __ldcg(&I->iB);
+        R.hasBox = __ldcg(&I->hasBox);
+        for (int k = 0; k < 4; k++) {
+            R.poly[k] = ldcg_cand(&I->poly[k]);
+            R.box[k] = __ldcg(&I->box[k]);
+        }
+    }
+    const long long first = R.lt * TILE;
+    const int c = (int)min((long long)TILE, R.setN - first);
+    R.nItems = c;
+    int sx = 0, si = 0;
+    unsigned bytes = 0u;
+    part_geo(R.g[0], R.setOff + first, c, 0, false, sx, si, bytes, (int)((reinterpret_cast<uintptr_t>(p.pts) >> 3) & 1),
+             0);
+    if (withPoly && R.K == 0) bytes = 0u;  // no segments: the tile is skipped
+    R.bytes = bytes;
+}
+
+__device__ void resolve_round_tile(const Params &p, TileRec &R, long long t, int S, long long L, int cur, int src) {
+    const long long v0 = t * TILE, v1 = min(v0 + (long long)TILE, L);
+    const long long *vs = p.vstart[cur];
+    const int *bl = p.bigList[cur];
+    const long long sA = upper_bound_ll(vs, (long long)S + 1, v0) - 1;
+    R.t = t;
+    R.nItems = (int)(v1 - v0);
+    R.valid = 1;
+    R.srcBuf = src;
+    int np = 1;
+    R.node[0] = __ldcg(&bl[sA]);
+    R.vstart[0] = __ldcg(&vs[sA]);
+    if (sA + 1 < S) {
+        const long long vb = __ldcg(&vs[sA + 1]);
+        if (vb < v1) {
+            np = 2;
+            R.node[1] = __ldcg(&bl[sA + 1]);
+            R.vstart[1] = vb;
+        }
+    }
+    R.np = np;
+    int sx = 0, si = 0;
+    unsigned bytes = 0u;
+    for (int part = 0; part < np; part++) {
+        const Node *N = &p.nodes[R.node[part]];
+        R.pstart[part] = __ldcg(&N->pstart);
+        R.count[part] = __ldcg(&N->count);
+        R.nh[part] = ldcg_cand(&N->h);
+        R.ne[part] = ldcg_cand(&N->e);
+        R.nc[part] = ldcg_cand(&N->c);
+        const long long fv = part ? R.vstart[1] : v0;
+        const long long lv = (part == 0 && np == 2) ? R.vstart[1] : v1;
+        const long long q0 = R.pstart[part] + (fv - R.vstart[part]);
+        const int c = (int)(lv - fv);
+        if (c < 0 || q0 < 0 || q0 + c > 2 * p.ncap) {  // guard: never copy outside the live buffer
+            set_err(p.ctl, E_INTERNAL);
+            R.valid = 0;
+        }
+        part_geo(R.g[part], q0, c, (int)(fv - v0), true, sx, si, bytes,
+                 (int)((reinterpret_cast<uintptr_t>(p.xy[src]) >> 3) & 1),
+                 (int)((reinterpret_cast<uintptr_t>(p.id[src]) >> 2) & 3));
+    }
+    R.bytes = R.valid ? bytes : 0u;
+}
+
+// Thread 0: start the copies of tile descriptor R into stage s.
+template <typename P>
+__device__ void issue_desc(const Params &p, RoundSmem<P> &sm, int s, const TileRec &R, bool set) {
+    mbar_expect_tx(&sm.mbar[s], R.bytes);
+    if (R.bytes == 0u) return;
+    if (set) {
+        bulk_g2s(&sm.stage[s].xy[0], p.pts + R.g[0].a0, R.bytes, &sm.mbar[s]);
+        return;
+    }
+    const float2 *gxy = p.xy[R.srcBuf];
+    const int *gid = p.id[R.srcBuf];
+    for (int part = 0; part < R.np; part++) {
+        const PartGeo &g = R.g[part];
+        if (g.a1 > g.a0) bulk_g2s(&sm.stage[s].xy[g.sx], gxy + g.a0, (unsigned)(g.a1 - g.a0) * 8u, &sm.mbar[s]);
+        if (g.b1 > g.b0) bulk_g2s(&sm.stage[s].id[g.si], gid + g.b0, (unsigned)(g.b1 - g.b0) * 4u, &sm.mbar[s]);
+    }
+}
+
+// Descriptor of the CTA's k-th tile of the current sequence.
+template <typename P> __device__ __forceinline__ TileRec &desc_of(RoundSmem<P> &sm, long long k) {
+    return sm.desc[(k / DB) & 1][k % DB];
+}
+
+// All threads: resolve the descriptors of the CTA's tiles k0 .. k0+DB-1.
+struct TileSeq {
+    long long first, step, cnt;
+    int kind;  // 0: set tiles (extremes), 1: set tiles with polygon (round 0), 2: round tiles
+    int S, cur, src;
+    long long L;
+};
+template <typename P> __device__ void resolve_batch(const Params &p, RoundSmem<P> &sm, const TileSeq &q, long long k0) {
+    __syncthreads();
+    const long long j = threadIdx.x;
+    if (j < DB && k0 + j < q.cnt) {
+        const long long t = q.first + (k0 + j) * q.step;
+        if (q.kind == 2)
+            resolve_round_tile(p, desc_of(sm, k0 + j), t, q.S, q.L, q.cur, q.src);
+        else
+            resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1);
     }
     __syncthreads();
 }
 
-template <typename P> __device__ void extremes_tile(const Params &p, RoundSmem<P> &sm, long long t) {
-    locate_tile(p, sm, t);
-    const int i = sm.inst;
-    const long long lt = sm.lt;
-    const Inst *I = &p.inst[i];
-    const long long off = __ldcg(&I->off), n = __ldcg(&I->n);
-    const int tiles = __ldcg(&I->tiles);
-    const long long tile0 = __ldcg(&I->tile0);
-    Ext e = ext_empty();
-#pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        const long long v = lt * TILE + (long long)k * NT + threadIdx.x;
-        if (v < n) {
-            const float2 q = __ldg(&p.pts[off + v]);
-            if (!isfinite(q.x) || !isfinite(q.y)) {
-                e.nonfinite = 1;
-            } else {
-                const int id = (int)v;
-                if (lex_less(q.x, q.y, id, e.a.x, e.a.y, e.a.idx)) e.a = mk_cand(q.x, q.y, id);
-                if (lex_greater(q.x, q.y, id, e.b.x, e.b.y, e.b.idx)) e.b = mk_cand(q.x, q.y, id);
-                if (lex_less(q.y, q.x, id, e.bot.y, e.bot.x, e.bot.idx)) e.bot = mk_cand(q.x, q.y, id);
-                if (lex_greater(q.y, q.x, id, e.top.y, e.top.x, e.top.idx)) e.top = mk_cand(q.x, q.y, id);
+// Start the pipeline: first batch of descriptors, then the first NS tiles.
+// The global data a phase copies with TMA was written by ordinary stores of
+// earlier phases (ordered by the grid barrier); one proxy fence per phase by
+// the issuing thread orders them before the async copies.  Stage reuse needs
+// none: the CTA barrier after the consumers' reads precedes every refill.
+template <typename P>
+__device__ void pipe_start(const Params &p, RoundSmem<P> &sm, const TileSeq &q, unsigned long long &gI) {
+    if (q.cnt <= 0) return;
+    if (threadIdx.x == 0) fence_proxy_async();
+    resolve_batch(p, sm, q, 0);
+    for (long long j = 0; j < min(q.cnt, (long long)NS); j++) {
+        if (threadIdx.x == 0) issue_desc(p, sm, (int)(gI % NS), desc_of(sm, j), q.kind != 2);
+        gI++;
+    }
+}
+
+// After tile k's points are in registers (and a barrier): refill its stage with tile k + NS.
+template <typename P>
+__device__ void pipe_refill(const Params &p, RoundSmem<P> &sm, const TileSeq &q, long long k, int s,
+                            unsigned long long &gI) {
+    const long long nk = k + NS;
+    if (nk >= q.cnt) return;
+    if (nk % DB == 0) resolve_batch(p, sm, q, nk);
+    if (threadIdx.x == 0) issue_desc(p, sm, s, desc_of(sm, nk), q.kind != 2);
+    gI++;
+}
+
+// Wait for every copy still in flight (used on the error path before leaving).
+template <typename P>
+__device__ void pipe_drain(const Params &p, RoundSmem<P> &sm, unsigned long long gI, unsigned long long gC) {
+    for (unsigned long long q = gC; q < gI; q++) {
+        unsigned it = 0;
+        while (!mbar_try_wait(&sm.mbar[q % NS], (unsigned)((q / NS) & 1ull)))
+            if (++it > SPIN_LIMIT) break;
+    }
+}
+
+// --------------------------------------------------------------------------
+// extremes (Sec. 4.2)
+// --------------------------------------------------------------------------
+// An axis-aligned box inside the closed initial polygon (K >= 3 vertices, CCW):
+// points in the closed box are never strictly right of an edge, so the
+// initial split can drop them with four comparisons.  Candidate: half-way
+// between the centroid and the four extreme points; every corner is verified
+// with the exact orientation test (shrunk towards the centroid on failure).
+__device__ __noinline__ int inner_box(const Cand (&poly)[4], int K, const Ext &a, float (&box)[4]) {
+    float cx = 0.f, cy = 0.f;
+    for (int k = 0; k < K; k++) {
+        cx += poly[k].x;
+        cy += poly[k].y;
+    }
+    cx /= (float)K;
+    cy /= (float)K;
+    float hx0 = 0.5f * (a.a.x - cx), hx1 = 0.5f * (a.b.x - cx);
+    float hy0 = 0.5f * (a.bot.y - cy), hy1 = 0.5f * (a.top.y - cy);
+    for (int tries = 0; tries < 4; tries++) {
+        const float bx[4] = {cx + hx0, cx + hx1, cy + hy0, cy + hy1};
+        bool ok = isfinite(bx[0]) && isfinite(bx[1]) && isfinite(bx[2]) && isfinite(bx[3]) && bx[0] <= bx[1] &&
+                  bx[2] <= bx[3];
+        for (int c = 0; c < 4 && ok; c++) {
+            const float px = (c & 1) ? bx[1] : bx[0], py = (c & 2) ? bx[3] : bx[2];
+            for (int k = 0; k < K && ok; k++) {
+                const Cand &u = poly[k], &v = poly[(k + 1) % K];
+                if (orient_exact(u.x, u.y, v.x, v.y, px, py) < 0) ok = false;
             }
         }
+        if (ok) {
+            for (int k = 0; k < 4; k++) box[k] = bx[k];
+            return 1;
+        }
+        hx0 *= 0.5f;
+        hx1 *= 0.5f;
+        hy0 *= 0.5f;
+        hy1 *= 0.5f;
     }
-    e = warp_ext_reduce(e);
+    return 0;
+}
+
+// Reduce this CTA's running extremes of set i, store them as the partial of
+// the CTA's first tile of that set, and let the CTA that completes the set's
+// tiles merge all partials into the initial polygon.
+template <typename P>
+__device__ __noinline__ void ext_flush(const Params &p, RoundSmem<P> &sm, Ext e, int i, long long segFirst, int segTiles) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    e = warp_ext_reduce(e);
+    __syncthreads();
     if (lane == 0) sm.wext[w] = e;
     __syncthreads();
     if (threadIdx.x == 0) {
         Ext r = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(r, sm.wext[k]);
-        st_ext(&p.text[t], r);
+        st_ext(&p.text[segFirst], r);
         __threadfence();
-        unsigned prev = atomicAdd(&p.inst[i].done, 1u);
-        sm.kflag = (prev == (unsigned)tiles - 1u);
+        const unsigned prev = atomicAdd(&p.inst[i].done, (unsigned)segTiles);
+        sm.kflag = (prev + (unsigned)segTiles == (unsigned)__ldcg(&p.inst[i].tiles));
         __threadfence();
     }
     __syncthreads();
     if (!sm.kflag) return;
-    // last tile of set i: merge all partials
+    const Inst *I = &p.inst[i];
+    const long long tile0 = __ldcg(&I->tile0);
+    const long long tiles = __ldcg(&I->tiles);
+    const long long T = __ldcg(&p.ctl->bigTiles), G = gridDim.x;
     Ext r = ext_empty();
-    for (int k = threadIdx.x; k < tiles; k += NT) ext_merge(r, ld_ext(&p.text[tile0 + k]));
+    if (threadIdx.x == 0) ext_merge(r, ld_ext(&p.text[tile0]));
+    for (long long b = threadIdx.x; b < G; b += NT) {
+        const long long c = b * T / G;  // chunk starts inside the set hold partials too
+        if (c > tile0 && c < tile0 + tiles) ext_merge(r, ld_ext(&p.text[c]));
+    }
     r = warp_ext_reduce(r);
     __syncthreads();
     if (lane == 0) sm.wext[w] = r;
@@ -464,8 +781,9 @@ template <typename P> __device__ void extremes_tile(const Params &p, RoundSmem<P
         Ext a = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(a, sm.wext[k]);
         Inst &W = p.inst[i];
-        int K = 0;
+        int K = 0, iB = 1, hasBox = 0;
         Cand poly[4];
+        float box[4] = {0.f, 0.f, 0.f, 0.f};
         int kind = I_BIG;
         if (a.nonfinite) {
             kind = I_NONFINITE;
@@ -476,270 +794,354 @@ template <typename P> __device__ void extremes_tile(const Params &p, RoundSmem<P
             const bool quad = (p.mode == 0);
             poly[K++] = a.a;
             if (quad && !same_xy(a.bot, a.a) && !same_xy(a.bot, a.b)) poly[K++] = a.bot;
+            iB = K;
             poly[K++] = a.b;
             if (quad && !same_xy(a.top, a.a) && !same_xy(a.top, a.b)) poly[K++] = a.top;
+            if (K >= 3) hasBox = inner_box(poly, K, a, box);
         }
         W.kind = kind;
         W.K = K;
+        W.iB = iB;
+        W.hasBox = hasBox;
+        for (int k = 0; k < 4; k++) W.box[k] = box[k];
         for (int k = 0; k < 4; k++) W.poly[k] = (k < K || (kind == I_DEGEN && k == 0)) ? poly[k] : no_cand();
         __threadfence();
     }
     __syncthreads();
 }
 
+template <typename P>
+__device__ __noinline__ bool phase_extremes(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC) {
+    const long long T = __ldcg(&p.ctl->bigTiles), G = gridDim.x;
+    const long long cb = (long long)blockIdx.x * T / G, ce = ((long long)blockIdx.x + 1) * T / G;
+    const long long cnt = ce - cb;
+    TileSeq q;
+    q.first = cb;
+    q.step = 1;
+    q.cnt = cnt;
+    q.kind = 0;
+    q.S = q.cur = q.src = 0;
+    q.L = 0;
+    pipe_start(p, sm, q, gI);
+    Ext acc = ext_empty();
+    int accInst = -1, segTiles = 0;
+    long long segFirst = 0;
+    QH_PROF_DECL;
+    for (long long k = 0; k < cnt; k++) {
+        const int s = (int)(gC % NS);
+        const unsigned par = (unsigned)((gC / NS) & 1ull);
+        gC++;
+        if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
+            pipe_drain(p, sm, gI, gC);
+            return false;
+        }
+        QH_PROF(0);
+        const TileRec &R = desc_of(sm, k);
+        const int inst = R.inst;
+        if (inst != accInst) {
+            if (accInst >= 0) ext_flush(p, sm, acc, accInst, segFirst, segTiles);
+            acc = ext_empty();
+            accInst = inst;
+            segFirst = R.t;
+            segTiles = 0;
+        }
+        const int nItems = R.nItems;
+        const long long base = R.lt * TILE;
+#pragma unroll
+        for (int kk = 0; kk < IPT; kk++) {
+            const int i = kk * NT + threadIdx.x;
+            if (i < nItems) {
+                const float2 q = fetch_xy(R, sm.stage[s], i, p.pts, true);
+                if (!isfinite(q.x) || !isfinite(q.y)) {
+                    acc.nonfinite = 1;
+                } else {
+                    const int id = (int)(base + i);
+                    if (lex_less(q.x, q.y, id, acc.a.x, acc.a.y, acc.a.idx)) acc.a = mk_cand(q.x, q.y, id);
+                    if (lex_greater(q.x, q.y, id, acc.b.x, acc.b.y, acc.b.idx)) acc.b = mk_cand(q.x, q.y, id);
+                    if (lex_less(q.y, q.x, id, acc.bot.y, acc.bot.x, acc.bot.idx)) acc.bot = mk_cand(q.x, q.y, id);
+                    if (lex_greater(q.y, q.x, id, acc.top.y, acc.top.x, acc.top.idx)) acc.top = mk_cand(q.x, q.y, id);
+                }
+            }
+        }
+        segTiles++;
+        QH_PROF(1);
+        __syncthreads();
+        QH_PROF(2);
+        pipe_refill(p, sm, q, k, s, gI);
+        QH_PROF(3);
+    }
+    if (accInst >= 0) ext_flush(p, sm, acc, accInst, segFirst, segTiles);
+    QH_PROF(4);
+    QH_PROF_FLUSH_AT(p.ctl, 8);
+    return true;
+}
+
 // --------------------------------------------------------------------------
 // round 0: the initial split
 // --------------------------------------------------------------------------
 template <typename P>
-__device__ void round0_tile(const Params &p, RoundSmem<P> &sm, long long t, int &exact_o, int &exact_c,
-                            long long &survivors) {
-    locate_tile(p, sm, t);
-    const int i = sm.inst;
-    const long long lt = sm.lt;
-    const Inst *I = &p.inst[i];
-    const int K = __ldcg(&I->K);
-    if (K == 0) return;  // degenerate or rejected set: no segments
-    const long long off = __ldcg(&I->off), n = __ldcg(&I->n);
-    const int tiles = __ldcg(&I->tiles);
-    if (threadIdx.x < 4) {
-        const int s = threadIdx.x;
-        if (s < K) {
-            const Cand u = ldcg_cand(&I->poly[s]);
-            const Cand v = ldcg_cand(&I->poly[(s + 1) % K]);
-            sm.edge[s] = make_edge<P>(u.x, u.y, v.x, v.y);
-            sm.vend[s][0] = v.x;
-            sm.vend[s][1] = v.y;
+__device__ __noinline__ bool phase_round0(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC,
+                             int &exact_o, int &exact_c, long long &survivors) {
+    const long long T = __ldcg(&p.ctl->bigTiles);
+    const long long first = blockIdx.x, step = gridDim.x;
+    const long long cnt = first < T ? (T - 1 - first) / step + 1 : 0;
+    TileSeq q;
+    q.first = first;
+    q.step = step;
+    q.cnt = cnt;
+    q.kind = 1;
+    q.S = q.cur = q.src = 0;
+    q.L = 0;
+    pipe_start(p, sm, q, gI);
+    QH_PROF_DECL;
+    for (long long kt = 0; kt < cnt; kt++) {
+        const int s = (int)(gC % NS);
+        const unsigned par = (unsigned)((gC / NS) & 1ull);
+        gC++;
+        QH_PROF(7);
+        if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
+            pipe_drain(p, sm, gI, gC);
+            return false;
         }
-    }
-    __syncthreads();
-
-    float x[IPT], y[IPT];
-    int idx[IPT], slot[IPT], rank[IPT];
-    P lo[IPT], hi[IPT];
+        QH_PROF(0);
+        const TileRec &R = desc_of(sm, kt);
+        const int K = R.K;
+        float x[IPT], y[IPT];
+        int idx[IPT], slot[IPT], rank[IPT];
+        P lo[IPT], hi[IPT];
+        const int nItems = R.nItems;
+        const long long base = R.lt * TILE;
 #pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        const long long v = lt * TILE + (long long)k * NT + threadIdx.x;
-        slot[k] = -1;
-        lo[k] = hi[k] = P(0);
-        x[k] = y[k] = 0.f;
-        idx[k] = (int)v;
-        if (v < n) {
-            const float2 q = __ldg(&p.pts[off + v]);
-            x[k] = q.x;
-            y[k] = q.y;
-            for (int s = 0; s < K; s++) {
-                if (right_of(sm.edge[s], sm.vend[s][0], sm.vend[s][1], q.x, q.y, lo[k], hi[k], exact_o)) {
-                    slot[k] = s;
+        for (int k = 0; k < IPT; k++) {
+            const int i = k * NT + threadIdx.x;
+            slot[k] = -1;
+            lo[k] = hi[k] = P(0);
+            x[k] = y[k] = 0.f;
+            idx[k] = (int)(base + i);
+            if (K > 0 && i < nItems) {
+                const float2 q = fetch_xy(R, sm.stage[s], i, p.pts, true);
+                x[k] = q.x;
+                y[k] = q.y;
+            }
+        }
+        if (threadIdx.x < K) {
+            const Cand u = R.poly[threadIdx.x], v = R.poly[(threadIdx.x + 1) % K];
+            sm.edge[threadIdx.x] = make_edge<P>(u.x, u.y, v.x, v.y);
+            sm.vend[threadIdx.x][0] = v.x;
+            sm.vend[threadIdx.x][1] = v.y;
+        } else if (threadIdx.x == 32 && K > 0) {
+            const Cand u = R.poly[0], v = R.poly[R.iB];
+            sm.edge[4] = make_edge<P>(u.x, u.y, v.x, v.y);
+            sm.vend[4][0] = v.x;
+            sm.vend[4][1] = v.y;
+        }
+        __syncthreads();
+        pipe_refill(p, sm, q, kt, s, gI);
+        QH_PROF(1);
+        if (K == 0) continue;  // degenerate or rejected set: no segments
+        const TileRec &C = R;
+        // A point lies strictly outside at most one edge of the initial polygon.
+        // Its side of the chord A->B tells which chain (A..B below, B..A above)
+        // can hold that edge; on the chord (or in the inner box) it is inside.
+        const int iB = C.iB, hasBox = C.hasBox;
+        const float bx0 = C.box[0], bx1 = C.box[1], by0 = C.box[2], by1 = C.box[3];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const int i = k * NT + threadIdx.x;
+            if (i >= nItems) continue;
+            const float px = x[k], py = y[k];
+            if (hasBox && px >= bx0 && px <= bx1 && py >= by0 && py <= by1) continue;
+            const Edge<P> &ch = sm.edge[4];
+            const Approx<P> o = orient_approx(ch, px, py);
+            const int sg = orient_sign(ch, sm.vend[4][0], sm.vend[4][1], px, py, o, exact_o);
+            if (sg == 0) continue;
+            const int e0 = sg < 0 ? 0 : iB, e1 = sg < 0 ? iB : K;
+            if (e1 - e0 == 1) {  // the chain is the chord itself: A->B below, B->A above
+                const DistIv<P> d = dist_interval(o);
+                slot[k] = e0;
+                if (sg < 0) {
+                    lo[k] = d.lo;
+                    hi[k] = d.hi;
+                } else {  // distance right of B->A is +orient(A, B, P)
+                    lo[k] = -d.hi;
+                    hi[k] = -d.lo;
+                }
+                continue;
+            }
+            for (int e = e0; e < e1; e++) {
+                if (right_of(sm.edge[e], sm.vend[e][0], sm.vend[e][1], px, py, lo[k], hi[k], exact_o)) {
+                    slot[k] = e;
                     break;
                 }
             }
         }
-    }
-    unsigned tot[4];
-    tile_ranks(slot, rank, tot, sm);
-    tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
+        QH_PROF(2);
+        unsigned tot[4];
+        tile_ranks(slot, rank, tot, sm);
+        QH_PROF(3);
+        tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
+        QH_PROF(4);
 
-    const unsigned epoch = 1u;
-    if (threadIdx.x == 0) {
-        Carry local;
-        for (int s = 0; s < 4; s++) {
-            local.cnt[s] = tot[s];
-            local.best[s] = sm.best[s];
-        }
-        Carry c;
-        bool ok = true;
-        if (lt == 0) {
-            publish(p, t, epoch, 2u, local, K);
-            for (int s = 0; s < 4; s++) {
-                c.cnt[s] = 0u;
-                c.best[s] = no_cand();
-            }
-        } else {
-            publish(p, t, epoch, 1u, local, K);
-            ok = lookback(p, t, epoch, K, sm, c, exact_c);
-            Carry inc = c;
-            carry_merge(inc, local, K, sm, exact_c);
-            publish(p, t, epoch, 2u, inc, K);
-        }
-        sm.carry = c;
-        sm.kflag = ok;
-        if (ok && lt == tiles - 1) {
-            Carry f = c;
-            carry_merge(f, local, K, sm, exact_c);
-            Inst *W = &p.inst[i];
-            for (int s = 0; s < K; s++) {
-                __stcg(&W->chCount[s], (int)f.cnt[s]);
-                stcg_cand(&W->chC[s], f.best[s]);
-            }
+        const long long t = C.t;
+        Inst *W = &p.inst[C.inst];
+        if (threadIdx.x < K)  // reserve this tile's range in each initial segment
+            sm.base[threadIdx.x] = tot[threadIdx.x] ? atomicAdd(&W->chCount[threadIdx.x], (int)tot[threadIdx.x]) : 0;
+        if (threadIdx.x == 32) {
+            store_tile_bests(p, t, sm.best);
             __threadfence();
+            sm.fflag[0] = atomicAdd(&W->done0, 1u) == (unsigned)C.tiles - 1u;
         }
-    }
-    __syncthreads();
-    if (!sm.kflag) return;
+        __syncthreads();
+        QH_PROF(5);
+        const long long off = C.setOff, n = C.setN;
 #pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        const int s = slot[k];
-        if (s < 0) continue;
-        const long long base = (s < 2 ? 0ll : p.ncap) + off;
-        const long long r = (long long)sm.carry.cnt[s] + rank[k];
-        const long long pos = (s & 1) ? base + n - 1 - r : base + r;
-        if (pos < base || pos >= base + n) {  // guard: never write outside the set's range
-            set_err(p.ctl, E_INTERNAL);
-            continue;
+        for (int k = 0; k < IPT; k++) {
+            const int q = slot[k];
+            if (q < 0) continue;
+            const long long b = (q < 2 ? 0ll : p.ncap) + off;
+            const long long rr = (long long)sm.base[q] + rank[k];
+            const long long pos = (q & 1) ? b + n - 1 - rr : b + rr;
+            if (pos < b || pos >= b + n) {  // guard: never write outside the set's range
+                set_err(p.ctl, E_INTERNAL);
+                continue;
+            }
+            __stcg(&p.xy[0][pos], make_float2(x[k], y[k]));
+            __stcg(&p.id[0][pos], idx[k]);
         }
-        __stcg(&p.xy[0][pos], make_float2(x[k], y[k]));
-        __stcg(&p.id[0][pos], idx[k]);
+        if (sm.fflag[0]) {  // last tile of the set: farthest point of every initial segment
+            __threadfence();
+            merge_parent_bests(p, sm, C.tile0, C.tile0 + C.tiles - 1, 0, K, 0, exact_c);
+            if (threadIdx.x < K) stcg_cand(&W->chC[threadIdx.x], sm.fin[threadIdx.x]);
+        }
+        if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
+        QH_PROF(6);
     }
-    if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
+    QH_PROF_FLUSH(p.ctl);
+    return true;
 }
 
 // --------------------------------------------------------------------------
 // round r >= 1
 // --------------------------------------------------------------------------
 template <typename P>
-__device__ void round_tile(const Params &p, RoundSmem<P> &sm, long long t, int r, int S, long long L, int cur,
-                           int &exact_o, int &exact_c, long long &survivors) {
+__device__ __noinline__ bool phase_round(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC, int r,
+                            int S, long long L, int cur, int &exact_o, int &exact_c, long long &survivors) {
     const int src = (r - 1) & 1, dst = r & 1;
-    const long long v0 = t * TILE;
-    const long long v1 = min(v0 + (long long)TILE, L);
-    const long long *vs = p.vstart[cur];
-    const int *bl = p.bigList[cur];
-    if (threadIdx.x == 0) {
-        const long long sA = upper_bound_ll(vs, (long long)S + 1, v0) - 1;
-        int np = 1;
-        sm.node[0] = __ldcg(&bl[sA]);
-        sm.vstart[0] = __ldcg(&vs[sA]);
-        if (sA + 1 < S && __ldcg(&vs[sA + 1]) < v1) {
-            np = 2;
-            sm.node[1] = __ldcg(&bl[sA + 1]);
-            sm.vstart[1] = __ldcg(&vs[sA + 1]);
+    const long long T = (L + TILE - 1) / TILE;
+    const long long first = blockIdx.x, step = gridDim.x;
+    const long long cnt = first < T ? (T - 1 - first) / step + 1 : 0;
+    TileSeq q;
+    q.first = first;
+    q.step = step;
+    q.cnt = cnt;
+    q.kind = 2;
+    q.S = S;
+    q.cur = cur;
+    q.src = src;
+    q.L = L;
+    pipe_start(p, sm, q, gI);
+    for (long long kt = 0; kt < cnt; kt++) {
+        const int s = (int)(gC % NS);
+        const unsigned par = (unsigned)((gC / NS) & 1ull);
+        gC++;
+        if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
+            pipe_drain(p, sm, gI, gC);
+            return false;
         }
-        sm.nparts = np;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * sm.nparts) {
-        const int part = threadIdx.x >> 1, which = threadIdx.x & 1;
-        const Node *N = &p.nodes[sm.node[part]];
-        const Cand h = ldcg_cand(&N->h), e = ldcg_cand(&N->e), c = ldcg_cand(&N->c);
-        const Cand u = which ? c : h;
-        const Cand v = which ? e : c;
-        sm.edge[2 * part + which] = make_edge<P>(u.x, u.y, v.x, v.y);
-        sm.vend[2 * part + which][0] = v.x;
-        sm.vend[2 * part + which][1] = v.y;
-        if (!which) {
-            sm.pstart[part] = __ldcg(&N->pstart);
-            sm.count[part] = __ldcg(&N->count);
-        }
-    }
-    __syncthreads();
-    const int np = sm.nparts;
-
-    float x[IPT], y[IPT];
-    int idx[IPT], slot[IPT], rank[IPT];
-    P lo[IPT], hi[IPT];
+        const TileRec &R = desc_of(sm, kt);
+        const int valid = R.valid, np = R.np, nItems = R.nItems;
+        float x[IPT], y[IPT];
+        int idx[IPT], slot[IPT], rank[IPT];
+        P lo[IPT], hi[IPT];
 #pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        const long long v = v0 + (long long)k * NT + threadIdx.x;
-        slot[k] = -1;
-        lo[k] = hi[k] = P(0);
-        x[k] = y[k] = 0.f;
-        idx[k] = -1;
-        if (v < v1) {
-            const int part = (np == 2 && v >= sm.vstart[1]) ? 1 : 0;
-            const long long phys = sm.pstart[part] + (v - sm.vstart[part]);
-            if (phys < 0 || phys >= 2 * p.ncap) {  // guard: never read outside the live buffer
-                set_err(p.ctl, E_INTERNAL);
+        for (int k = 0; k < IPT; k++) {
+            const int i = k * NT + threadIdx.x;
+            slot[k] = -1;
+            lo[k] = hi[k] = P(0);
+            x[k] = y[k] = 0.f;
+            idx[k] = -1;
+            if (valid && i < nItems) {
+                const float2 q = fetch_xy(R, sm.stage[s], i, p.xy[src], false);
+                x[k] = q.x;
+                y[k] = q.y;
+                idx[k] = fetch_id(R, sm.stage[s], i, p.id[src]);
+            }
+        }
+        if (threadIdx.x < 2 * np) {
+            const int part = threadIdx.x >> 1, which = threadIdx.x & 1;
+            const Cand u = which ? R.nc[part] : R.nh[part];
+            const Cand v = which ? R.ne[part] : R.nc[part];
+            sm.edge[threadIdx.x] = make_edge<P>(u.x, u.y, v.x, v.y);
+            sm.vend[threadIdx.x][0] = v.x;
+            sm.vend[threadIdx.x][1] = v.y;
+        }
+        __syncthreads();
+        pipe_refill(p, sm, q, kt, s, gI);
+        if (!valid) continue;
+        const TileRec &C = R;
+        const long long vB = np == 2 ? (long long)C.g[1].vofs : (long long)TILE;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const int i = k * NT + threadIdx.x;
+            if (i < nItems) {
+                const int s0 = (i >= vB) ? 2 : 0;
+                if (right_of(sm.edge[s0], sm.vend[s0][0], sm.vend[s0][1], x[k], y[k], lo[k], hi[k], exact_o))
+                    slot[k] = s0;
+                else if (right_of(sm.edge[s0 + 1], sm.vend[s0 + 1][0], sm.vend[s0 + 1][1], x[k], y[k], lo[k], hi[k],
+                                  exact_o))
+                    slot[k] = s0 + 1;
+            }
+        }
+        unsigned tot[4];
+        tile_ranks(slot, rank, tot, sm);
+        tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
+
+        const long long t = C.t;
+        if (threadIdx.x < 2 * np) {  // reserve this tile's range in each child
+            const int q = threadIdx.x;
+            Node *N = &p.nodes[C.node[q >> 1]];
+            sm.base[q] = tot[q] ? atomicAdd(&N->chCount[q & 1], (int)tot[q]) : 0;
+        }
+        if (threadIdx.x == 32) {
+            store_tile_bests(p, t, sm.best);
+            __threadfence();
+            for (int part = 0; part < 2; part++) {
+                int last = 0;
+                if (part < np) {
+                    const long long vs = C.vstart[part], cn = C.count[part];
+                    const unsigned nt = (unsigned)((vs + cn - 1) / TILE - vs / TILE + 1);
+                    last = atomicAdd(&p.nodes[C.node[part]].tdone, 1u) == nt - 1u;
+                }
+                sm.fflag[part] = last;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const int q = slot[k];
+            if (q < 0) continue;
+            const int part = q >> 1;
+            const long long ps = C.pstart[part], cn = C.count[part];
+            const long long rr = (long long)sm.base[q] + rank[k];
+            const long long pos = (q & 1) ? ps + cn - 1 - rr : ps + rr;
+            if (pos < ps || pos >= ps + cn || pos >= 2 * p.ncap) {
+                set_err(p.ctl, E_INTERNAL);  // guard: a child never leaves its parent's range
                 continue;
             }
-            const float2 q = __ldcg(&p.xy[src][phys]);
-            x[k] = q.x;
-            y[k] = q.y;
-            idx[k] = __ldcg(&p.id[src][phys]);
-            const int s0 = 2 * part;
-            if (right_of(sm.edge[s0], sm.vend[s0][0], sm.vend[s0][1], q.x, q.y, lo[k], hi[k], exact_o))
-                slot[k] = s0;
-            else if (right_of(sm.edge[s0 + 1], sm.vend[s0 + 1][0], sm.vend[s0 + 1][1], q.x, q.y, lo[k], hi[k],
-                              exact_o))
-                slot[k] = s0 + 1;
+            __stcg(&p.xy[dst][pos], make_float2(x[k], y[k]));
+            __stcg(&p.id[dst][pos], idx[k]);
         }
-    }
-    unsigned tot[4];
-    tile_ranks(slot, rank, tot, sm);
-    tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
-
-    const unsigned epoch = (unsigned)r + 1u;
-    if (threadIdx.x == 0) {
-        Carry la, lb;
-        for (int s = 0; s < 2; s++) {
-            la.cnt[s] = tot[s];
-            la.best[s] = sm.best[s];
-            lb.cnt[s] = tot[2 + s];
-            lb.best[s] = sm.best[2 + s];
-        }
-        for (int s = 2; s < 4; s++) {
-            la.cnt[s] = lb.cnt[s] = 0u;
-            la.best[s] = lb.best[s] = no_cand();
-        }
-        const bool contA = sm.vstart[0] < v0;
-        Carry c;
-        for (int s = 0; s < 4; s++) {
-            c.cnt[s] = 0u;
-            c.best[s] = no_cand();
-        }
-        bool ok = true;
-        if (np == 2)
-            publish(p, t, epoch, 2u, lb, 2);
-        else if (!contA)
-            publish(p, t, epoch, 2u, la, 2);
-        else
-            publish(p, t, epoch, 1u, la, 2);
-        if (contA) {
-            ok = lookback(p, t, epoch, 2, sm, c, exact_c);
-            if (np == 1) {
-                Carry inc = c;
-                carry_merge(inc, la, 2, sm, exact_c);
-                publish(p, t, epoch, 2u, inc, 2);
-            }
-        }
-        sm.carry = c;
-        sm.kflag = ok;
-        if (ok) {
-            if (sm.vstart[0] + sm.count[0] <= v1) {  // part A ends in this tile
-                Carry f = c;
-                carry_merge(f, la, 2, sm, exact_c);
-                Node *N = &p.nodes[sm.node[0]];
-                for (int s = 0; s < 2; s++) {
-                    __stcg(&N->chCount[s], (int)f.cnt[s]);
-                    stcg_cand(&N->chC[s], f.best[s]);
-                }
-            }
-            if (np == 2 && sm.vstart[1] + sm.count[1] <= v1) {  // part B starts and ends here
-                Node *N = &p.nodes[sm.node[1]];
-                for (int s = 0; s < 2; s++) {
-                    __stcg(&N->chCount[s], (int)lb.cnt[s]);
-                    stcg_cand(&N->chC[s], lb.best[s]);
-                }
-            }
+        for (int part = 0; part < np; part++) {
+            if (!sm.fflag[part]) continue;  // this tile closes the parent: farthest points of its children
             __threadfence();
+            const long long vs = C.vstart[part], cn = C.count[part];
+            const long long ta = vs / TILE, tb = (vs + cn - 1) / TILE;
+            merge_parent_bests(p, sm, ta, tb, (vs % TILE) != 0 ? 2 : 0, 2, 2 * part, exact_c);
+            if (threadIdx.x < 2) stcg_cand(&p.nodes[C.node[part]].chC[threadIdx.x], sm.fin[threadIdx.x]);
         }
+        if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
     }
-    __syncthreads();
-    if (!sm.kflag) return;
-#pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        const int s = slot[k];
-        if (s < 0) continue;
-        const int part = s >> 1;
-        const long long rr = (long long)(part == 0 ? sm.carry.cnt[s] : 0u) + rank[k];
-        const long long pos = (s & 1) ? sm.pstart[part] + sm.count[part] - 1 - rr : sm.pstart[part] + rr;
-        if (pos < sm.pstart[part] || pos >= sm.pstart[part] + sm.count[part] || pos >= 2 * p.ncap) {
-            set_err(p.ctl, E_INTERNAL);  // guard: a child never leaves its parent's range
-            continue;
-        }
-        __stcg(&p.xy[dst][pos], make_float2(x[k], y[k]));
-        __stcg(&p.id[dst][pos], idx[k]);
-    }
-    if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
+    return true;
 }
 
 // --------------------------------------------------------------------------
@@ -799,7 +1201,7 @@ __device__ __forceinline__ int node_kind(int count, int cut) {
     return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
 }
 
-template <typename P> __device__ void build_level0(const Params &p, RoundSmem<P> &sm) {
+template <typename P> __device__ __noinline__ void build_level0(const Params &p, RoundSmem<P> &sm) {
     long long *scr = sm.scanTmp;
     const int nBig = __ldcg(&p.ctl->nBig);
     long long carry = 0;
@@ -835,6 +1237,9 @@ template <typename P> __device__ void build_level0(const Params &p, RoundSmem<P>
                 __stcg(&N->level, 0);
                 __stcg(&N->child, -1);
                 __stcg(&N->inner, 0);
+                __stcg(&N->chCount[0], 0);
+                __stcg(&N->chCount[1], 0);
+                __stcg(&N->tdone, 0u);
             }
         }
         carry += tot;
@@ -850,7 +1255,7 @@ template <typename P> __device__ void build_level0(const Params &p, RoundSmem<P>
     build_biglist(p, sm, 0, (int)carry, 0);
 }
 
-template <typename P> __device__ void build_level(const Params &p, RoundSmem<P> &sm, int r) {
+template <typename P> __device__ __noinline__ void build_level(const Params &p, RoundSmem<P> &sm, int r) {
     const int S = __ldcg(&p.ctl->S);
     const int cur = __ldcg(&p.ctl->cur);
     const int base = __ldcg(&p.ctl->nNodes);
@@ -880,6 +1285,9 @@ template <typename P> __device__ void build_level(const Params &p, RoundSmem<P> 
             __stcg(&N->level, r);
             __stcg(&N->child, -1);
             __stcg(&N->inner, 0);
+            __stcg(&N->chCount[0], 0);
+            __stcg(&N->chCount[1], 0);
+            __stcg(&N->tdone, 0u);
         }
     }
     __threadfence();
@@ -896,47 +1304,51 @@ template <typename P> __device__ void build_level(const Params &p, RoundSmem<P> 
 // --------------------------------------------------------------------------
 // the kernel
 // --------------------------------------------------------------------------
-template <typename P> __global__ void __launch_bounds__(NT, 2) rounds_kernel(Params p) {
-    __shared__ RoundSmem<P> sm;
+template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(Params p) {
+    extern __shared__ __align__(128) unsigned char rounds_smem_raw[];
+    RoundSmem<P> &sm = *reinterpret_cast<RoundSmem<P> *>(rounds_smem_raw);
     unsigned phase = 0, donePhase = 0;
     int exact_o = 0, exact_c = 0;
     long long surv = 0;
+    unsigned long long gI = 0, gC = 0;
 
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++) mbar_init(&sm.mbar[s], 1u);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    stamp(p.ctl, 0);
     if (blockIdx.x == 0) prep(p, sm);
     if (!grid_sync(p.ctl, phase)) goto out;
+    stamp(p.ctl, 1);
 
-    {
-        const long long T = __ldcg(&p.ctl->bigTiles);
-        for (long long t = blockIdx.x; t < T; t += gridDim.x) extremes_tile(p, sm, t);
-    }
+    phase_extremes(p, sm, gI, gC);
     if (!grid_sync(p.ctl, phase)) goto out;
+    stamp(p.ctl, 2);
 
-    {
-        const long long T = __ldcg(&p.ctl->bigTiles);
-        for (long long t = blockIdx.x; t < T; t += gridDim.x) round0_tile(p, sm, t, exact_o, exact_c, surv);
-        if (threadIdx.x == 0 && surv) atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
-        surv = 0;
-        if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level0(p, sm);
-    }
+    phase_round0(p, sm, gI, gC, exact_o, exact_c, surv);
+    if (threadIdx.x == 0 && surv) atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
+    surv = 0;
+    if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level0(p, sm);
     if (!grid_sync(p.ctl, phase)) goto out;
+    stamp(p.ctl, 3);
 
     for (int r = 1;; r++) {
         const int S = __ldcg(&p.ctl->S);
         if (S == 0) break;
         const long long L = __ldcg(&p.ctl->L);
-        const long long T = __ldcg(&p.ctl->tiles);
         const int cur = __ldcg(&p.ctl->cur);
-        if (T > p.maxTiles) {
+        if ((L + TILE - 1) / TILE > p.maxTiles) {
             if (blockIdx.x == 0 && threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
             break;
         }
-        for (long long t = blockIdx.x; t < T; t += gridDim.x)
-            round_tile(p, sm, t, r, S, L, cur, exact_o, exact_c, surv);
+        phase_round(p, sm, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
         if (threadIdx.x == 0 && surv)
             atomicAdd((unsigned long long *)&p.ctl->live[min(r, MAX_GEN - 1)], (unsigned long long)surv);
         surv = 0;
         if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level(p, sm, r);
         if (!grid_sync(p.ctl, phase)) goto out;
+        stamp(p.ctl, 3 + r);
     }
 out:
     {
@@ -954,19 +1366,35 @@ out:
     }
 }
 
+template <typename P> static cudaError_t set_rounds_smem() {
+    return cudaFuncSetAttribute(rounds_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(RoundSmem<P>));
+}
+
 cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s) {
     void *args[] = {(void *)&p};
-    if (prec)
-        return cudaLaunchCooperativeKernel((void *)rounds_kernel<double>, dim3(grid), dim3(NT), args, 0, s);
-    return cudaLaunchCooperativeKernel((void *)rounds_kernel<float>, dim3(grid), dim3(NT), args, 0, s);
+    cudaError_t e;
+    if (prec) {
+        e = set_rounds_smem<double>();
+        if (e != cudaSuccess) return e;
+        return cudaLaunchCooperativeKernel((void *)rounds_kernel<double>, dim3(grid), dim3(NT), args,
+                                           sizeof(RoundSmem<double>), s);
+    }
+    e = set_rounds_smem<float>();
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((void *)rounds_kernel<float>, dim3(grid), dim3(NT), args,
+                                       sizeof(RoundSmem<float>), s);
 }
 
 int rounds_max_ctas_per_sm(int prec) {
     int b = 0;
-    if (prec)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rounds_kernel<double>, NT, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rounds_kernel<float>, NT, 0);
+    if (prec) {
+        if (set_rounds_smem<double>() != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rounds_kernel<double>, NT, sizeof(RoundSmem<double>));
+    } else {
+        if (set_rounds_smem<float>() != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rounds_kernel<float>, NT, sizeof(RoundSmem<float>));
+    }
     return b;
 }
 
