@@ -75,6 +75,11 @@ typedef struct {
                                    split, then grid-wide rounds 1.. (device clock) */
     uint64_t section_cycles[16];/* per-tile section cycle sums of CTA thread 0; zero unless the
                                    library was built with -DQH_PROFILE */
+    int64_t grid_points;        /* points of the sets tiled by the grid-wide kernel (read twice:
+                                   extreme points and initial split) */
+    int64_t grid_read;          /* live points read by grid-wide rounds after the initial split */
+    int64_t grid_written;       /* live points written by the initial split and grid-wide rounds */
+    int64_t small_points;       /* points handled by the block finisher (small segments and sets) */
 } qh_stats;
 
 /*

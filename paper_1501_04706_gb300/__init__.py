@@ -46,7 +46,9 @@ class _Stats(ctypes.Structure):
                 ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32),
                 ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
                 ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5),
-                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 16)]
+                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 16),
+                ("grid_points", ctypes.c_int64), ("grid_read", ctypes.c_int64), ("grid_written", ctypes.c_int64),
+                ("small_points", ctypes.c_int64)]
 
 
 _lib = None
@@ -134,7 +136,9 @@ class Plan:
                 "live": [int(v) for v in s.live[: min(g, MAX_GEN)]], "exact_orient": int(s.exact_orient),
                 "exact_compare": int(s.exact_compare), "phase_ms": [float(v) for v in s.phase_ms],
                 "grid_phase_us": [float(v) for v in s.grid_phase_us if v > 0],
-                "section_cycles": [int(v) for v in s.section_cycles]}
+                "section_cycles": [int(v) for v in s.section_cycles], "grid_points": int(s.grid_points),
+                "grid_read": int(s.grid_read), "grid_written": int(s.grid_written),
+                "small_points": int(s.small_points)}
 
 
 def _points_tensor(points):

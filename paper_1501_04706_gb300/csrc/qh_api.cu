@@ -389,6 +389,10 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
     out->generations = last < 0 ? 1 : last + 2;
     for (int k = 0; k < 16; k++) out->section_cycles[k] = c.prof[k];
     out->exact_orient = (int64_t)c.exactOrient;
+    out->grid_points = c.bigPoints;
+    out->grid_read = c.gridRead;
+    out->grid_written = c.gridWritten;
+    out->small_points = c.smallPoints;
     out->exact_compare = (int64_t)c.exactCmp;
     for (int k = 0; k < 16; k++) {
         const int hi = k + 1;

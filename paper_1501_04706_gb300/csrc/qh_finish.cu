@@ -299,6 +299,7 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     if (isNode) {
         const Node *N = &p.nodes[id];
         m = N->count;
+        if (threadIdx.x == 0) atomicAdd((unsigned long long *)&p.ctl->smallPoints, (unsigned long long)m);
         const int buf = N->buf;
         pstart = N->pstart;
         src = p.xy[buf] + pstart;

@@ -99,6 +99,10 @@ struct Ctl {
     int nSmall;          // small-segment queue length
     unsigned finTicket;
     int rounds;          // grid-wide rounds run after the initial split
+    long long bigPoints;     // points of the sets tiled by the grid-wide kernel
+    long long gridRead;      // live points read by grid-wide rounds r >= 1
+    long long gridWritten;   // live points written by the initial split and the grid-wide rounds
+    long long smallPoints;   // points handled by the block finisher
     int gens;            // generations run (max over sets)
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;

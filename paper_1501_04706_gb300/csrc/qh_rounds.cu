@@ -466,7 +466,7 @@ __device__ __noinline__ void merge_parent_bests(const Params &p, RoundSmem<P> &s
 // --------------------------------------------------------------------------
 template <typename P> __device__ __noinline__ void prep(const Params &p, RoundSmem<P> &sm) {
     long long *scr = sm.scanTmp;
-    long long carryBig = 0, carrySmall = 0, carryTiles = 0;
+    long long carryBig = 0, carrySmall = 0, carryTiles = 0, bigPts = 0, smallPts = 0;
     for (int base = 0; base < p.numSets; base += NT) {
         const int i = base + threadIdx.x;
         long long off = 0, n = 0;
@@ -492,6 +492,11 @@ template <typename P> __device__ __noinline__ void prep(const Params &p, RoundSm
         long long xb = block_excl_scan<long long, NT>(kind == I_BIG ? 1 : 0, scr, tb);
         long long xs = block_excl_scan<long long, NT>(kind == I_SMALL ? 1 : 0, scr, ts);
         long long xt = block_excl_scan<long long, NT>(tiles, scr, tt);
+        long long tbp, tsp;
+        block_excl_scan<long long, NT>(kind == I_BIG ? n : 0, scr, tbp);
+        block_excl_scan<long long, NT>(kind == I_SMALL ? n : 0, scr, tsp);
+        bigPts += tbp;
+        smallPts += tsp;
         if (i < p.numSets) {
             Inst &I = p.inst[i];
             I.off = off;
@@ -523,6 +528,8 @@ template <typename P> __device__ __noinline__ void prep(const Params &p, RoundSm
         p.ctl->nBig = (int)carryBig;
         p.ctl->nSmallInst = (int)carrySmall;
         p.ctl->bigTiles = carryTiles;
+        p.ctl->bigPoints = bigPts;
+        p.ctl->smallPoints = smallPts;
         p.ctl->S = 0;
         p.ctl->L = 0;
         p.ctl->tiles = 0;
@@ -1327,7 +1334,10 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     stamp(p.ctl, 2);
 
     phase_round0(p, sm, gI, gC, exact_o, exact_c, surv);
-    if (threadIdx.x == 0 && surv) atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
+    if (threadIdx.x == 0 && surv) {
+        atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
+        atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
+    }
     surv = 0;
     if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level0(p, sm);
     if (!grid_sync(p.ctl, phase)) goto out;
@@ -1343,8 +1353,11 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
             break;
         }
         phase_round(p, sm, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
-        if (threadIdx.x == 0 && surv)
+        if (threadIdx.x == 0 && surv) {
             atomicAdd((unsigned long long *)&p.ctl->live[min(r, MAX_GEN - 1)], (unsigned long long)surv);
+            atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->gridRead += L;
         surv = 0;
         if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level(p, sm, r);
         if (!grid_sync(p.ctl, phase)) goto out;
