@@ -150,6 +150,27 @@ qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *of
 qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
                          int32_t *host_out_count, qh_stream_t stream);
 
+/*
+ * qh_hull2d_noalloc -- the hull of one set (same output as qh_hull2d: quadrilateral
+ * initial split, FP32 filtered predicates with exact fallback) for callers that
+ * must not allocate device memory when they need a hull: real-time loops that
+ * cannot afford cudaMalloc's implicit device synchronisation, or plug-ins whose
+ * host application owns the device-memory budget.  The paper has no counterpart:
+ * this is an interface addition.
+ *   points, n, out_idx, out_count, stream: as for qh_hull2d_p.
+ *   n must not exceed QH_NOALLOC_MAX_POINTS; larger sets return QH_ERR_CAPACITY
+ *   without touching the device.
+ * Scratch: one fixed array in the library's device image (about 16 MB on every
+ * GPU that loads the library, held until the process exits); no cudaMalloc,
+ * cudaFree or other allocating call is made.  The first call on a device looks up
+ * the array's address for that device (it must come before any stream capture).
+ * All calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race and corrupt each other's results; serialise them.
+ */
+#define QH_NOALLOC_MAX_POINTS 262144
+qh_status qh_hull2d_noalloc(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                            qh_stream_t stream);
+
 /* Statistics of the plan's last call; synchronizes the plan's last stream. */
 qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out);
 

@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libqh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu"]
+SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu", "qh_noalloc.cu"]
 HEADERS = ["qh_internal.cuh", "qh_predicates.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
