@@ -73,7 +73,7 @@ typedef struct {
     float phase_ms[5];          /* with timing on: grid rounds, finisher, emit, copy, total */
     float grid_phase_us[16];    /* inside the grid-wide kernel: set prep, extreme points, initial
                                    split, then grid-wide rounds 1.. (device clock) */
-    uint64_t section_cycles[16];/* per-tile section cycle sums of CTA thread 0; zero unless the
+    uint64_t section_cycles[32];/* per-tile section cycle sums of CTA thread 0; zero unless the
                                    library was built with -DQH_PROFILE */
     int64_t grid_points;        /* points of the sets tiled by the grid-wide kernel (read twice:
                                    extreme points and initial split) */
@@ -98,7 +98,8 @@ qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags);
 
 /*
  * Tuning knobs.  cutover: segments with at most this many points are finished
- * by one thread block in shared memory (2048 <= cutover <= 4096).  timing: 1
+ * by one thread block in shared memory; it must equal 4096 (the grid-wide
+ * tile size, so a tile never spans more than two segments).  timing: 1
  * records CUDA events between the kernels so qh_plan_get_stats can report
  * per-phase times.  grid_ctas_per_sm: 0 = occupancy maximum.
  */

@@ -387,7 +387,7 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
         if (c.live[g] > 0) last = g;
     }
     out->generations = last < 0 ? 1 : last + 2;
-    for (int k = 0; k < 16; k++) out->section_cycles[k] = c.prof[k];
+    for (int k = 0; k < 32; k++) out->section_cycles[k] = c.prof[k];
     out->exact_orient = (int64_t)c.exactOrient;
     out->grid_points = c.bigPoints;
     out->grid_read = c.gridRead;

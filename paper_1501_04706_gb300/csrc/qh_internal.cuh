@@ -18,12 +18,12 @@ namespace qh {
 #define QH_NT 256
 #endif
 #ifndef QH_MINB
-#define QH_MINB 4
+#define QH_MINB 2
 #endif
 constexpr int NT = QH_NT;          // threads per CTA of the grid-wide kernel
 constexpr int MINB = QH_MINB;      // CTAs per SM the grid-wide kernel is built for
 constexpr int NWARP = NT / 32;
-constexpr int IPT = 4;             // points per thread per tile (warp-striped rows)
+constexpr int IPT = 16;            // points per thread per tile (warp-striped rows)
 constexpr int TILE = NT * IPT;     // points per tile
 constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
 constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
@@ -56,8 +56,7 @@ struct Inst {
     unsigned done;     // tiles of the extreme-point pass finished (atomic)
     unsigned done0;    // tiles of the initial split finished (atomic)
     Cand poly[4];      // initial polygon, CCW, starting at the lexicographic minimum
-    int iB, hasBox;    // index of the rightmost vertex B in poly; inner box valid
-    float box[4];      // x0, x1, y0, y1 of an axis-aligned box inside the closed polygon
+    int iB, pad0;      // index of the rightmost vertex B in poly
     int chCount[4];    // points of each initial segment: output cursors during the split (atomic)
     Cand chC[4];       // farthest point of each initial segment
 };
@@ -107,7 +106,7 @@ struct Ctl {
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;
     unsigned long long tphase[MAX_LEVELS + 4];  // %globaltimer at the kernel start and after each grid barrier
-    unsigned long long prof[16];                // section cycle counters (profiling builds only)
+    unsigned long long prof[32];                // section cycle counters (profiling builds only)
 };
 
 struct Params {
@@ -304,6 +303,9 @@ __device__ __forceinline__ float fkey_inv(unsigned k) {
 }
 __device__ __forceinline__ unsigned pkey(float f) { return fkey(f); }
 __device__ __forceinline__ unsigned pkey(double d) { return fkey(__double2float_rd(d)); }
+// Key of an upper bound (rounded up to float).
+__device__ __forceinline__ unsigned pkey_up(float f) { return fkey(f); }
+__device__ __forceinline__ unsigned pkey_up(double d) { return fkey(__double2float_ru(d)); }
 
 // Host launchers (defined in the .cu files).
 cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);

@@ -14,10 +14,12 @@
 //     |det - D| <= (4u + O(u^2)) (|l| + |r|),
 // l and r being the two rounded products.  We use 5u * fl(|l| + |r|), which
 // covers the O(u^2) terms and the rounding of the bound itself.  In FP32 the
-// bound also needs |l| + |r| >= 2^-96 (so products that underflowed contribute
-// at most 2^-149 each, far below the slack u * 2^-96) and a finite value
-// (overflow); otherwise the point goes to the exact path.  In FP64 the products
-// of float differences neither underflow nor overflow.
+// bound gets an absolute floor of 2^-140: a product that underflowed is off by
+// at most 2^-150 and a subnormal difference is exact, so below |l| + |r| =
+// 2^-96 the floor covers every error and above it the slack u (|l| + |r|)
+// does.  A sum |l| + |r| that overflowed (or is NaN: inf * 0) marks the value
+// unusable and the point goes to the exact path.  In FP64 the products of
+// float differences neither underflow nor overflow.
 //
 // Exact path: every float x float product is exact in FP64; the sign of a sum of
 // such products is the sign of the top non-zero component of the nonoverlapping
@@ -121,14 +123,17 @@ QH_HD double add_up(double a, double b) {
 template <typename P> struct Lim;
 template <> struct Lim<float> {
     static QH_HD float errc() { return 5.0f * 0x1p-24f; }
-    static QH_HD float smin() { return 0x1p-96f; }
+    static QH_HD float efloor() { return 0x1p-140f; }
     static QH_HD float smax() { return FLT_MAX; }
 };
 template <> struct Lim<double> {
     static QH_HD double errc() { return 5.0 * 0x1p-53; }
-    static QH_HD double smin() { return 0.0; }
+    static QH_HD double efloor() { return 0.0; }
     static QH_HD double smax() { return DBL_MAX; }
 };
+
+QH_HD float rmax(float a, float b) { return a > b ? a : b; }
+QH_HD double rmax(double a, double b) { return a > b ? a : b; }
 
 // A directed edge u->v with its rounded direction, the constants every
 // orientation test against it reuses.
@@ -161,8 +166,8 @@ template <typename P> QH_HD Approx<P> orient_approx(const Edge<P> &e, float px, 
     Approx<P> o;
     o.det = rsub(l, r);
     P s = radd(l < P(0) ? -l : l, r < P(0) ? -r : r);
-    o.err = rmul(s, Lim<P>::errc());
-    o.ok = (s >= Lim<P>::smin()) && (s <= Lim<P>::smax());
+    o.err = rmax(rmul(s, Lim<P>::errc()), Lim<P>::efloor());
+    o.ok = s <= Lim<P>::smax();
     return o;
 }
 

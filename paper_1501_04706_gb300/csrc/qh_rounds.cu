@@ -38,17 +38,21 @@
 
 namespace qh {
 
-constexpr int NS = 3;          // pipeline stages per CTA
-constexpr int DB = 16;         // tile descriptors resolved per batch (one thread per tile)
+constexpr int NS = 2;          // pipeline stages per CTA
+constexpr int DB = 8;          // tile descriptors resolved per batch (one thread per tile)
+constexpr int CLS_NONE = 15;
 constexpr int CAND_CAP = 128;  // farthest-point candidates kept per tile before the fallback
 
 // Items of one segment inside a tile: physical range [q0, q0 + c) of the
-// source buffer, first tile-local item vofs; [a0, a1) / [b0, b1) are the
-// 16-byte aligned interiors copied by TMA to stage offsets sx / si (the
-// ragged ends, at most one point on each side, are read directly).
+// source buffer, first tile-local item vofs.  The copies take the 16-byte
+// blocks that hold the range: na points from a0 to stage offset sx and nb ids
+// from b0 to stage offset si, so item i of the part sits at stage xy[i + dx]
+// and id[i + di].  A 16-byte aligned block holding a byte of a valid element
+// lies inside one memory page, so the rounded-out copy reads mapped memory
+// only; the elements it adds at either end are never used.
 struct PartGeo {
-    long long q0, a0, a1, b0, b1;
-    int c, vofs, sx, si;
+    long long q0, a0, b0;
+    int c, vofs, na, nb, sx, si, dx, di;
 };
 
 struct TileRec {
@@ -58,8 +62,7 @@ struct TileRec {
     int srcBuf;      // live buffer read by a round tile
     // round 0 / extremes: the set
     long long lt, setOff, setN, tile0;
-    int tiles, K, iB, hasBox;
-    float box[4];
+    int tiles, K, iB;
     Cand poly[4];
     // rounds: the (at most two) parent segments
     int node[2], count[2];
@@ -68,21 +71,42 @@ struct TileRec {
     PartGeo g[2];
 };
 
+constexpr int STAGE_PAD = 16;  // room for the rounded-out ends of two parts
 struct StageBuf {
-    float2 xy[TILE];
-    int id[TILE];
+    float2 xy[TILE + STAGE_PAD];
+    int id[TILE + STAGE_PAD];
+};
+
+// The CTA's running farthest-point candidates for the parent it is working on
+// (a run of consecutive tiles of one parent: a set in the initial split, a
+// segment in the rounds).
+struct RunAcc {
+    int node;          // parent (set index in the initial split, node index in the rounds); -1: none
+    int nslot;         // child slots of the parent
+    int tiles;         // tiles merged into this run
+    int total;         // tiles of the parent
+    int slotBase;      // record slots of this run: tbest[4 * first + slotBase + s]
+    int slotBase0;     // record slot base of the parent's first run
+    int edgeOff;       // the parent's edges in the working set: edge[edgeOff + s]
+    int pad;
+    long long first;   // tile holding this run's record
+    long long ta, tb;  // first and last tile of the parent
+    Cand best[4];
 };
 
 template <typename P> struct RoundSmem {
     unsigned long long mbar[NS];
+    RunAcc run;
     TileRec desc[2][DB];  // descriptors of the CTA's tiles, double-buffered by batch
     // tile working set
-    Edge<P> edge[5];   // per slot; edge[4]: the chord A->B of the initial split
-    float vend[5][2];
+    Edge<P> edge[4];   // per slot: the edge a point of the slot lies strictly right of
+    float vend[4][2];
     int kflag;
-    unsigned long long warpTot[IPT * NWARP];
-    unsigned long long tileTot;
+    unsigned warpCnt[NWARP][4];  // pass 1: points per warp and slot
+    int warpOff[NWARP][4];       // their offsets inside the tile's reservation
+    int tot[4];                  // points per slot in the tile
     unsigned maxLo[4];
+    unsigned tk[4];  // extremes: keys of the tile's min x, max x, min y, max y
     int ncand;
     Cand best[4];
     Cand fin[4];
@@ -93,8 +117,17 @@ template <typename P> struct RoundSmem {
     Cand wbest[NWARP][4];
     Cand cand[CAND_CAP];
     unsigned char cslot[CAND_CAP];
+    unsigned clsPack[2][NT];     // 4-bit slot of every item of the tile (CLS_NONE: discarded)
     alignas(128) StageBuf stage[NS];
 };
+
+// The CTA's working set.  Functions that are not inlined take it from the
+// symbol rather than through a reference, so that its accesses stay
+// shared-memory loads and stores instead of generic ones.
+extern __shared__ __align__(128) unsigned char rounds_smem_raw[];
+template <typename P> __device__ __forceinline__ RoundSmem<P> &round_smem() {
+    return *reinterpret_cast<RoundSmem<P> *>(rounds_smem_raw);
+}
 
 // --------------------------------------------------------------------------
 // TMA / mbarrier helpers
@@ -141,48 +174,35 @@ template <typename P> __device__ __forceinline__ bool pipe_wait(const Params &p,
 }
 
 // xyPhase / idPhase: element offset of the array base from a 16-byte boundary
-// (0/1 float2, 0..3 int), so that the copied interior is 16-byte aligned in memory.
+// (0/1 float2, 0..3 int), so that every copy starts and ends on a 16-byte
+// boundary in memory.
 __device__ __forceinline__ void part_geo(PartGeo &g, long long q0, int c, int vofs, bool withId, int &sx, int &si,
                                          unsigned &bytes, int xyPhase, int idPhase) {
     g.q0 = q0;
     g.c = c;
     g.vofs = vofs;
-    const long long end = q0 + c;
-    long long a0 = q0 + ((q0 + xyPhase) & 1), a1 = end - ((end + xyPhase) & 1);
-    if (a1 < a0) a1 = a0;
-    g.a0 = a0;
-    g.a1 = a1;
+    g.a0 = g.b0 = q0;
+    g.na = g.nb = 0;
     g.sx = sx;
-    sx += (int)(a1 - a0);
-    bytes += (unsigned)(a1 - a0) * 8u;
+    g.si = si;
+    g.dx = sx - vofs;
+    g.di = si - vofs;
+    if (c <= 0) return;
+    const long long end = q0 + c;
+    const long long a0 = q0 - ((q0 + xyPhase) & 1), a1 = end + ((end + xyPhase) & 1);
+    g.a0 = a0;
+    g.na = (int)(a1 - a0);
+    g.dx = sx + (int)(q0 - a0) - vofs;
+    sx += g.na;
+    bytes += (unsigned)g.na * 8u;
     if (withId) {
-        long long b0 = q0 + ((4 - ((q0 + idPhase) & 3)) & 3), b1 = end - ((end + idPhase) & 3);
-        if (b1 < b0) b1 = b0;
+        const long long b0 = q0 - ((q0 + idPhase) & 3), b1 = end + ((4 - ((end + idPhase) & 3)) & 3);
         g.b0 = b0;
-        g.b1 = b1;
-        g.si = si;
-        si += (int)(b1 - b0);
-        bytes += (unsigned)(b1 - b0) * 4u;
-    } else {
-        g.b0 = g.b1 = 0;
-        g.si = 0;
+        g.nb = (int)(b1 - b0);
+        g.di = si + (int)(q0 - b0) - vofs;
+        si += g.nb;
+        bytes += (unsigned)g.nb * 4u;
     }
-}
-
-__device__ __forceinline__ int part_of(const TileRec &R, int i) { return (R.np == 2 && i >= R.g[1].vofs) ? 1 : 0; }
-
-__device__ __forceinline__ float2 fetch_xy(const TileRec &R, const StageBuf &S, int i, const float2 *gxy,
-                                           bool readOnly) {
-    const PartGeo &g = R.g[part_of(R, i)];
-    const long long q = g.q0 + (i - g.vofs);
-    if (q >= g.a0 && q < g.a1) return S.xy[g.sx + (int)(q - g.a0)];
-    return readOnly ? __ldg(&gxy[q]) : __ldcg(&gxy[q]);
-}
-__device__ __forceinline__ int fetch_id(const TileRec &R, const StageBuf &S, int i, const int *gid) {
-    const PartGeo &g = R.g[part_of(R, i)];
-    const long long q = g.q0 + (i - g.vofs);
-    if (q >= g.b0 && q < g.b1) return S.id[g.si + (int)(q - g.b0)];
-    return __ldcg(&gid[q]);
 }
 
 // --------------------------------------------------------------------------
@@ -276,53 +296,6 @@ __device__ __forceinline__ bool last_cta(Ctl *ctl, unsigned &donePhase, int *fla
 // --------------------------------------------------------------------------
 // per-tile ranks and farthest points
 // --------------------------------------------------------------------------
-// slot[k] in {-1, 0..3} for the item of row k; rank[k] receives its exclusive
-// rank among the tile's items of the same slot, in tile order; tot[] the totals.
-template <typename P>
-__device__ __forceinline__ void tile_ranks(const int (&slot)[IPT], int (&rank)[IPT], unsigned (&tot)[4],
-                                           RoundSmem<P> &sm) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        unsigned long long packed = 0ull;
-        int r = 0;
-#pragma unroll
-        for (int s = 0; s < 4; s++) {
-            unsigned b = __ballot_sync(0xffffffffu, slot[k] == s);
-            if (slot[k] == s) r = __popc(b & lt);
-            packed |= (unsigned long long)__popc(b) << (16 * s);
-        }
-        rank[k] = r;
-        if (lane == 0) sm.warpTot[k * NWARP + w] = packed;
-    }
-    __syncthreads();
-    if (w == 0) {
-        constexpr int E = IPT * NWARP;
-        constexpr int PER = E / 32;
-        unsigned long long v[PER], s = 0ull;
-#pragma unroll
-        for (int i = 0; i < PER; i++) {
-            v[i] = sm.warpTot[lane * PER + i];
-            s += v[i];
-        }
-        unsigned long long inc = warp_incl_scan(s);
-        unsigned long long ex = inc - s;
-#pragma unroll
-        for (int i = 0; i < PER; i++) {
-            sm.warpTot[lane * PER + i] = ex;
-            ex += v[i];
-        }
-        if (lane == 31) sm.tileTot = inc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < IPT; k++)
-        if (slot[k] >= 0) rank[k] += (int)((sm.warpTot[k * NWARP + w] >> (16 * slot[k])) & 0xffffull);
-#pragma unroll
-    for (int s = 0; s < 4; s++) tot[s] = (unsigned)((sm.tileTot >> (16 * s)) & 0xffffull);
-}
-
 // Merge candidate b into a for the chord of slot s (exact order).
 template <typename P>
 __device__ __forceinline__ void cand_merge(Cand &a, const Cand &b, int s, const RoundSmem<P> &sm, int &exact_c) {
@@ -335,79 +308,6 @@ __device__ __forceinline__ void cand_merge(Cand &a, const Cand &b, int s, const 
     const DistIv<P> da = dist_interval(orient_approx(e, a.x, a.y));
     const DistIv<P> db = dist_interval(orient_approx(e, b.x, b.y));
     if (farther(e, sm.vend[s][0], sm.vend[s][1], b.x, b.y, b.idx, db, a.x, a.y, a.idx, da, exact_c)) a = b;
-}
-
-// Farthest point of each slot within the tile, exactly: the largest lower
-// bound per slot, then every item whose upper bound reaches it is a candidate,
-// and thread s picks the best candidate of slot s with the exact order.  When
-// more than CAND_CAP items are candidates (massive exact ties), every thread
-// reduces its own candidates and the warps combine them with the exact order.
-template <typename P>
-__device__ __forceinline__ void tile_farthest(const int (&slot)[IPT], const float (&x)[IPT], const float (&y)[IPT],
-                                              const int (&idx)[IPT], const P (&lo)[IPT], const P (&hi)[IPT],
-                                              RoundSmem<P> &sm, int &exact_c) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x < 4) sm.maxLo[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) sm.ncand = 0;
-    __syncthreads();
-    unsigned mk[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int k = 0; k < IPT; k++) {
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-            if (slot[k] == s) mk[s] = max(mk[s], max(pkey(lo[k]), 1u));
-    }
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        unsigned v = __reduce_max_sync(0xffffffffu, mk[s]);
-        if (lane == 0 && v != 0u) atomicMax(&sm.maxLo[s], v);
-    }
-    __syncthreads();
-    bool cand[IPT];
-#pragma unroll
-    for (int k = 0; k < IPT; k++) {
-        cand[k] = false;
-        if (slot[k] >= 0) {
-            const P thr = (P)fkey_inv(sm.maxLo[slot[k]]);
-            if (hi[k] >= thr) {
-                cand[k] = true;
-                int j = atomicAdd(&sm.ncand, 1);
-                if (j < CAND_CAP) {
-                    sm.cand[j] = mk_cand(x[k], y[k], idx[k]);
-                    sm.cslot[j] = (unsigned char)slot[k];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const int nc = sm.ncand;
-    if (nc <= CAND_CAP) {
-        if (threadIdx.x < 4) {
-            const int s = threadIdx.x;
-            Cand b = no_cand();
-            for (int j = 0; j < nc; j++)
-                if (sm.cslot[j] == s) cand_merge(b, sm.cand[j], s, sm, exact_c);
-            sm.best[s] = b;
-        }
-    } else {
-#pragma unroll 1
-        for (int s = 0; s < 4; s++) {
-            Cand b = no_cand();
-#pragma unroll
-            for (int k = 0; k < IPT; k++)
-                if (cand[k] && slot[k] == s) cand_merge(b, mk_cand(x[k], y[k], idx[k]), s, sm, exact_c);
-            for (int d = 16; d >= 1; d >>= 1) cand_merge(b, shfl_cand(b, lane ^ d), s, sm, exact_c);
-            if (lane == 0) sm.wbest[w][s] = b;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            const int s = threadIdx.x;
-            Cand b = no_cand();
-            for (int j = 0; j < NWARP; j++) cand_merge(b, sm.wbest[j][s], s, sm, exact_c);
-            sm.best[s] = b;
-        }
-    }
-    __syncthreads();
 }
 
 // Classify a point against an edge: returns true when strictly right, with the
@@ -427,26 +327,40 @@ __device__ __forceinline__ bool right_of(const Edge<P> &e, float vx, float vy, f
 }
 
 // --------------------------------------------------------------------------
-// per-tile farthest points and their merge per parent
+// farthest points per parent: runs of tiles and their merge
 // --------------------------------------------------------------------------
-// Thread of warp 1: the tile's own farthest points, read by the parent's last tile.
-__device__ __forceinline__ void store_tile_bests(const Params &p, long long t, const Cand (&b)[4]) {
-    for (int s = 0; s < 4; s++) stcg_cand(&p.tbest[4 * t + s], b[s]);
+// Every CTA works on a contiguous chunk of tiles, so a parent (a set in the
+// initial split, a segment in the rounds) is split between CTAs only at chunk
+// starts.  A CTA keeps the exact best candidate of every child over its run of
+// tiles of one parent and publishes it once, as a record in the run's first
+// tile; the publication that completes the parent's tile count merges the
+// parent's records.
+
+// Chunk of tiles of CTA b: [floor(b T / G), floor((b + 1) T / G)).
+__device__ __forceinline__ long long chunk_start(long long b, long long T, long long G) { return b * T / G; }
+// The chunk holding tile t: the largest b with chunk_start(b) <= t.
+__device__ __forceinline__ long long chunk_of(long long t, long long T, long long G) {
+    return min(((t + 1) * G + T - 1) / T - 1, G - 1);
 }
 
-// Exact farthest point of each of the nslot children of a parent whose points
-// span tiles [ta, tb]: merge of the per-tile bests (tile ta reads its slots
-// from slotBase0, the others from 0) with the chords sm.edge[edgeOff ..
-// edgeOff + nslot).  Whole CTA; result in sm.fin.
+// Farthest point of every child of a parent spanning tiles [ta, tb] -> sm.fin.
+// The parent's runs start at ta (record slots slotBase0..) and at every chunk
+// start inside (ta, tb] (slots 0..), each holding the exact best of its tiles.
 template <typename P>
-__device__ __noinline__ void merge_parent_bests(const Params &p, RoundSmem<P> &sm, long long ta, long long tb, int slotBase0,
-                                   int nslot, int edgeOff, int &exact_c) {
+__device__ __noinline__ void merge_runs(const Params &p, long long ta, long long tb, int slotBase0, int nslot,
+                                        int edgeOff, long long T, int &exact_c) {
+    RoundSmem<P> &sm = round_smem<P>();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long G = gridDim.x;
     Cand b[4] = {no_cand(), no_cand(), no_cand(), no_cand()};
-    for (long long u = ta + threadIdx.x; u <= tb; u += NT) {
-        const int base = (u == ta) ? slotBase0 : 0;
-        for (int s = 0; s < nslot; s++)
-            cand_merge(b[s], ldcg_cand(&p.tbest[4 * u + base + s]), edgeOff + s, sm, exact_c);
+    if (threadIdx.x == 0)
+        for (int s = 0; s < nslot; s++) b[s] = ldcg_cand(&p.tbest[4 * ta + slotBase0 + s]);
+    const long long c0 = chunk_of(ta, T, G), c1 = chunk_of(tb, T, G);
+    for (long long c = c0 + 1 + threadIdx.x; c <= c1; c += NT) {
+        const long long st = chunk_start(c, T, G);
+        if (st > ta && st < chunk_start(c + 1, T, G))  // a non-empty chunk starting inside the parent
+            for (int s = 0; s < nslot; s++)
+                cand_merge(b[s], ldcg_cand(&p.tbest[4 * st + s]), edgeOff + s, sm, exact_c);
     }
     for (int s = 0; s < nslot; s++) {
         for (int d = 16; d >= 1; d >>= 1) cand_merge(b[s], shfl_cand(b[s], lane ^ d), edgeOff + s, sm, exact_c);
@@ -461,10 +375,60 @@ __device__ __noinline__ void merge_parent_bests(const Params &p, RoundSmem<P> &s
     __syncthreads();
 }
 
+// Publish the CTA's run (record + tile count on the parent's counter); the
+// publication that completes the parent's tiles merges all its runs and stores
+// the children's farthest points.  kind 1: a set of the initial split; 2: a
+// segment of the rounds.  Uniform over the CTA.
+template <typename P>
+__device__ __noinline__ void flush_run(const Params &p, int kind, long long T, int &exact_c) {
+    RoundSmem<P> &sm = round_smem<P>();
+    RunAcc &ra = sm.run;
+    const int nslot = ra.nslot;
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < nslot; s++) stcg_cand(&p.tbest[4 * ra.first + ra.slotBase + s], ra.best[s]);
+        __threadfence();
+        unsigned *cnt = kind == 1 ? &p.inst[ra.node].done0 : &p.nodes[ra.node].tdone;
+        const unsigned old = atomicAdd(cnt, (unsigned)ra.tiles);
+        sm.fflag[0] = old + (unsigned)ra.tiles == (unsigned)ra.total;
+    }
+    __syncthreads();
+    if (sm.fflag[0]) {
+        __threadfence();
+        merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
+        if (threadIdx.x < nslot) {
+            Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
+            stcg_cand(dstC, sm.fin[threadIdx.x]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ra.node = -1;
+    __syncthreads();
+}
+
+// Start a run of parent `node` at tile t (thread 0 sets the fields; the caller
+// synchronises before they are read).
+__device__ __forceinline__ void run_start(RunAcc &ra, int node, int nslot, long long t, int slotBase, int edgeOff,
+                                          long long ta, long long tb, int slotBase0) {
+    if (threadIdx.x < 4) ra.best[threadIdx.x] = no_cand();
+    if (threadIdx.x == 0) {
+        ra.node = node;
+        ra.nslot = nslot;
+        ra.tiles = 0;
+        ra.total = (int)(tb - ta + 1);
+        ra.slotBase = slotBase;
+        ra.slotBase0 = slotBase0;
+        ra.edgeOff = edgeOff;
+        ra.first = t;
+        ra.ta = ta;
+        ra.tb = tb;
+    }
+}
+
 // --------------------------------------------------------------------------
 // prep: classify sets (CTA 0)
 // --------------------------------------------------------------------------
-template <typename P> __device__ __noinline__ void prep(const Params &p, RoundSmem<P> &sm) {
+template <typename P> __device__ __noinline__ void prep(const Params &p) {
+    RoundSmem<P> &sm = round_smem<P>();
     long long *scr = sm.scanTmp;
     long long carryBig = 0, carrySmall = 0, carryTiles = 0, bigPts = 0, smallPts = 0;
     for (int base = 0; base < p.numSets; base += NT) {
@@ -562,14 +526,11 @@ __device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool 
     R.tiles = __ldcg(&I->tiles);
     R.K = 0;
     R.iB = 1;
-    R.hasBox = 0;
     if (withPoly) {
         R.K = __ldcg(&I->K);
         R.iB = __ldcg(&I->iB);
-        R.hasBox = __ldcg(&I->hasBox);
         for (int k = 0; k < 4; k++) {
             R.poly[k] = ldcg_cand(&I->poly[k]);
-            R.box[k] = __ldcg(&I->box[k]);
         }
     }
     const long long first = R.lt * TILE;
@@ -606,6 +567,12 @@ __device__ void resolve_round_tile(const Params &p, TileRec &R, long long t, int
     R.np = np;
     int sx = 0, si = 0;
     unsigned bytes = 0u;
+    {  // no second part unless set below: an empty one at the stage start
+        PartGeo &g1 = R.g[1];
+        g1.q0 = g1.a0 = g1.b0 = 0;
+        g1.c = g1.na = g1.nb = g1.sx = g1.si = g1.dx = g1.di = 0;
+        g1.vofs = TILE;
+    }
     for (int part = 0; part < np; part++) {
         const Node *N = &p.nodes[R.node[part]];
         R.pstart[part] = __ldcg(&N->pstart);
@@ -630,19 +597,21 @@ __device__ void resolve_round_tile(const Params &p, TileRec &R, long long t, int
 
 // Thread 0: start the copies of tile descriptor R into stage s.
 template <typename P>
-__device__ void issue_desc(const Params &p, RoundSmem<P> &sm, int s, const TileRec &R, bool set) {
+__device__ void issue_desc(const Params &p, int s, const TileRec &R, bool set) {
+    RoundSmem<P> &sm = round_smem<P>();
     mbar_expect_tx(&sm.mbar[s], R.bytes);
     if (R.bytes == 0u) return;
     if (set) {
-        bulk_g2s(&sm.stage[s].xy[0], p.pts + R.g[0].a0, R.bytes, &sm.mbar[s]);
+        const PartGeo &g = R.g[0];
+        bulk_g2s(&sm.stage[s].xy[g.sx], p.pts + g.a0, (unsigned)g.na * 8u, &sm.mbar[s]);
         return;
     }
     const float2 *gxy = p.xy[R.srcBuf];
     const int *gid = p.id[R.srcBuf];
     for (int part = 0; part < R.np; part++) {
         const PartGeo &g = R.g[part];
-        if (g.a1 > g.a0) bulk_g2s(&sm.stage[s].xy[g.sx], gxy + g.a0, (unsigned)(g.a1 - g.a0) * 8u, &sm.mbar[s]);
-        if (g.b1 > g.b0) bulk_g2s(&sm.stage[s].id[g.si], gid + g.b0, (unsigned)(g.b1 - g.b0) * 4u, &sm.mbar[s]);
+        if (g.na > 0) bulk_g2s(&sm.stage[s].xy[g.sx], gxy + g.a0, (unsigned)g.na * 8u, &sm.mbar[s]);
+        if (g.nb > 0) bulk_g2s(&sm.stage[s].id[g.si], gid + g.b0, (unsigned)g.nb * 4u, &sm.mbar[s]);
     }
 }
 
@@ -658,7 +627,8 @@ struct TileSeq {
     int S, cur, src;
     long long L;
 };
-template <typename P> __device__ void resolve_batch(const Params &p, RoundSmem<P> &sm, const TileSeq &q, long long k0) {
+template <typename P> __device__ void resolve_batch(const Params &p, const TileSeq &q, long long k0) {
+    RoundSmem<P> &sm = round_smem<P>();
     __syncthreads();
     const long long j = threadIdx.x;
     if (j < DB && k0 + j < q.cnt) {
@@ -677,30 +647,33 @@ template <typename P> __device__ void resolve_batch(const Params &p, RoundSmem<P
 // the issuing thread orders them before the async copies.  Stage reuse needs
 // none: the CTA barrier after the consumers' reads precedes every refill.
 template <typename P>
-__device__ void pipe_start(const Params &p, RoundSmem<P> &sm, const TileSeq &q, unsigned long long &gI) {
+__device__ void pipe_start(const Params &p, const TileSeq &q, unsigned long long &gI) {
+    RoundSmem<P> &sm = round_smem<P>();
     if (q.cnt <= 0) return;
     if (threadIdx.x == 0) fence_proxy_async();
-    resolve_batch(p, sm, q, 0);
+    resolve_batch<P>(p, q, 0);
     for (long long j = 0; j < min(q.cnt, (long long)NS); j++) {
-        if (threadIdx.x == 0) issue_desc(p, sm, (int)(gI % NS), desc_of(sm, j), q.kind != 2);
+        if (threadIdx.x == 0) issue_desc<P>(p, (int)(gI % NS), desc_of(sm, j), q.kind != 2);
         gI++;
     }
 }
 
 // After tile k's points are in registers (and a barrier): refill its stage with tile k + NS.
 template <typename P>
-__device__ void pipe_refill(const Params &p, RoundSmem<P> &sm, const TileSeq &q, long long k, int s,
+__device__ void pipe_refill(const Params &p, const TileSeq &q, long long k, int s,
                             unsigned long long &gI) {
+    RoundSmem<P> &sm = round_smem<P>();
     const long long nk = k + NS;
     if (nk >= q.cnt) return;
-    if (nk % DB == 0) resolve_batch(p, sm, q, nk);
-    if (threadIdx.x == 0) issue_desc(p, sm, s, desc_of(sm, nk), q.kind != 2);
+    if (nk % DB == 0) resolve_batch<P>(p, q, nk);
+    if (threadIdx.x == 0) issue_desc<P>(p, s, desc_of(sm, nk), q.kind != 2);
     gI++;
 }
 
 // Wait for every copy still in flight (used on the error path before leaving).
 template <typename P>
-__device__ void pipe_drain(const Params &p, RoundSmem<P> &sm, unsigned long long gI, unsigned long long gC) {
+__device__ void pipe_drain(const Params &p, unsigned long long gI, unsigned long long gC) {
+    RoundSmem<P> &sm = round_smem<P>();
     for (unsigned long long q = gC; q < gI; q++) {
         unsigned it = 0;
         while (!mbar_try_wait(&sm.mbar[q % NS], (unsigned)((q / NS) & 1ull)))
@@ -711,50 +684,15 @@ __device__ void pipe_drain(const Params &p, RoundSmem<P> &sm, unsigned long long
 // --------------------------------------------------------------------------
 // extremes (Sec. 4.2)
 // --------------------------------------------------------------------------
-// An axis-aligned box inside the closed initial polygon (K >= 3 vertices, CCW):
-// points in the closed box are never strictly right of an edge, so the
-// initial split can drop them with four comparisons.  Candidate: half-way
-// between the centroid and the four extreme points; every corner is verified
-// with the exact orientation test (shrunk towards the centroid on failure).
-__device__ __noinline__ int inner_box(const Cand (&poly)[4], int K, const Ext &a, float (&box)[4]) {
-    float cx = 0.f, cy = 0.f;
-    for (int k = 0; k < K; k++) {
-        cx += poly[k].x;
-        cy += poly[k].y;
-    }
-    cx /= (float)K;
-    cy /= (float)K;
-    float hx0 = 0.5f * (a.a.x - cx), hx1 = 0.5f * (a.b.x - cx);
-    float hy0 = 0.5f * (a.bot.y - cy), hy1 = 0.5f * (a.top.y - cy);
-    for (int tries = 0; tries < 4; tries++) {
-        const float bx[4] = {cx + hx0, cx + hx1, cy + hy0, cy + hy1};
-        bool ok = isfinite(bx[0]) && isfinite(bx[1]) && isfinite(bx[2]) && isfinite(bx[3]) && bx[0] <= bx[1] &&
-                  bx[2] <= bx[3];
-        for (int c = 0; c < 4 && ok; c++) {
-            const float px = (c & 1) ? bx[1] : bx[0], py = (c & 2) ? bx[3] : bx[2];
-            for (int k = 0; k < K && ok; k++) {
-                const Cand &u = poly[k], &v = poly[(k + 1) % K];
-                if (orient_exact(u.x, u.y, v.x, v.y, px, py) < 0) ok = false;
-            }
-        }
-        if (ok) {
-            for (int k = 0; k < 4; k++) box[k] = bx[k];
-            return 1;
-        }
-        hx0 *= 0.5f;
-        hx1 *= 0.5f;
-        hy0 *= 0.5f;
-        hy1 *= 0.5f;
-    }
-    return 0;
-}
 
 // Reduce this CTA's running extremes of set i, store them as the partial of
 // the CTA's first tile of that set, and let the CTA that completes the set's
 // tiles merge all partials into the initial polygon.
 template <typename P>
-__device__ __noinline__ void ext_flush(const Params &p, RoundSmem<P> &sm, Ext e, int i, long long segFirst, int segTiles) {
+__device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long segFirst, int segTiles) {
+    RoundSmem<P> &sm = round_smem<P>();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    QH_PROF_DECL;
     e = warp_ext_reduce(e);
     __syncthreads();
     if (lane == 0) sm.wext[w] = e;
@@ -770,6 +708,7 @@ __device__ __noinline__ void ext_flush(const Params &p, RoundSmem<P> &sm, Ext e,
     }
     __syncthreads();
     if (!sm.kflag) return;
+    QH_PROF(0);
     const Inst *I = &p.inst[i];
     const long long tile0 = __ldcg(&I->tile0);
     const long long tiles = __ldcg(&I->tiles);
@@ -780,17 +719,19 @@ __device__ __noinline__ void ext_flush(const Params &p, RoundSmem<P> &sm, Ext e,
         const long long c = b * T / G;  // chunk starts inside the set hold partials too
         if (c > tile0 && c < tile0 + tiles) ext_merge(r, ld_ext(&p.text[c]));
     }
+    QH_PROF(1);
     r = warp_ext_reduce(r);
+    QH_PROF(2);
     __syncthreads();
     if (lane == 0) sm.wext[w] = r;
     __syncthreads();
+    QH_PROF(3);
     if (threadIdx.x == 0) {
         Ext a = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(a, sm.wext[k]);
         Inst &W = p.inst[i];
-        int K = 0, iB = 1, hasBox = 0;
+        int K = 0, iB = 1;
         Cand poly[4];
-        float box[4] = {0.f, 0.f, 0.f, 0.f};
         int kind = I_BIG;
         if (a.nonfinite) {
             kind = I_NONFINITE;
@@ -804,21 +745,282 @@ __device__ __noinline__ void ext_flush(const Params &p, RoundSmem<P> &sm, Ext e,
             iB = K;
             poly[K++] = a.b;
             if (quad && !same_xy(a.top, a.a) && !same_xy(a.top, a.b)) poly[K++] = a.top;
-            if (K >= 3) hasBox = inner_box(poly, K, a, box);
         }
         W.kind = kind;
         W.K = K;
         W.iB = iB;
-        W.hasBox = hasBox;
-        for (int k = 0; k < 4; k++) W.box[k] = box[k];
         for (int k = 0; k < 4; k++) W.poly[k] = (k < K || (kind == I_DEGEN && k == 0)) ? poly[k] : no_cand();
         __threadfence();
+        QH_PROF(6);
+    }
+    __syncthreads();
+    QH_PROF(7);
+}
+
+// --------------------------------------------------------------------------
+// two-pass tile engine (initial split and grid-wide rounds)
+// --------------------------------------------------------------------------
+// Thread t owns items j * NT + t (j < IPT) of the tile, all read from the TMA
+// stage.  Pass 1 classifies them, keeps their slots packed in two registers
+// (4 bits per item), counts the points of every slot per thread (8-bit
+// fields) and keeps, per slot, the largest lower distance bound.  One
+// reservation per (tile, slot) on the child's cursor then gives every warp its
+// output range, and pass 2 writes the survivors (ranks from warp ballots, so
+// stores are coalesced) and collects the candidates whose upper bound reaches
+// the slot's largest lower bound.
+
+// Record the slot c (CLS_NONE: discarded) of item j (a compile-time index
+// after unrolling) with the keys of its distance bounds.
+__device__ __forceinline__ void note_item(int j, int c, unsigned klo, unsigned khi, unsigned &cp0, unsigned &cp1,
+                                          unsigned &cnt, unsigned (&mlo)[4], unsigned (&mhi)[4]) {
+    if (j < 8)
+        cp0 |= (unsigned)c << (4 * j);
+    else
+        cp1 |= (unsigned)c << (4 * (j - 8));
+    cnt += c < 4 ? 1u << (8 * c) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        mlo[q] = c == q ? max(mlo[q], klo) : mlo[q];
+        mhi[q] = c == q ? max(mhi[q], khi) : mhi[q];
+    }
+}
+
+// The same for an item j known only at run time whose slot was CLS_NONE.
+__device__ __forceinline__ void renote_item(int j, int c, unsigned klo, unsigned khi, unsigned &cp0, unsigned &cp1,
+                                            unsigned &cnt, unsigned (&mlo)[4], unsigned (&mhi)[4]) {
+    const unsigned sh = 4u * (unsigned)(j & 7);
+    const unsigned m = ~(15u << sh) | ((unsigned)c << sh);
+    if (j < 8)
+        cp0 &= m;
+    else
+        cp1 &= m;
+    if (c != CLS_NONE) {
+        cnt += 1u << (8 * c);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (c == q) {
+                mlo[q] = max(mlo[q], klo);
+                mhi[q] = max(mhi[q], khi);
+            }
+    }
+}
+
+__device__ __forceinline__ int item_cls(int j, unsigned cp0, unsigned cp1) {
+    return (int)(((j < 8 ? cp0 : cp1) >> (4 * (j & 7))) & 15u);
+}
+
+// Filter decisions of one orientation: certainly strictly right / certainly left.
+template <typename P> struct Side {
+    bool r, l;
+};
+template <typename P> __device__ __forceinline__ Side<P> side_of(const Approx<P> &o) {
+    Side<P> d;
+    d.r = o.ok && o.det < -o.err;
+    d.l = o.ok && o.det > o.err;
+    return d;
+}
+
+// Classification against two candidate edges e0, e1 of which a point can be
+// strictly right of at most one (the first and second child of a segment in
+// the rounds; the lower- and upper-chain edge of the initial polygon in the
+// split).  Filter only: the slot (CLS_NONE when right of neither) with its
+// distance bounds; unsure when a decision needs the exact predicate.
+template <typename P>
+__device__ __forceinline__ int classify_fast(const RoundSmem<P> &sm, int e0, int e1, float px, float py, P &lo, P &hi,
+                                             bool &unsure) {
+    const Approx<P> oa = orient_approx(sm.edge[e0], px, py);
+    const Approx<P> ob = orient_approx(sm.edge[e1], px, py);
+    const Side<P> a = side_of(oa), b = side_of(ob);
+    const DistIv<P> d = dist_interval(a.r ? oa : ob);
+    lo = d.lo;
+    hi = d.hi;
+    unsure = !(a.r | b.r) & (!a.l | !b.l);
+    return unsure ? CLS_NONE : (a.r ? e0 : (b.r ? e1 : CLS_NONE));
+}
+
+// The same with exact decisions (the filter's undecided cases).
+template <typename P>
+__device__ __noinline__ int classify_exact(int e0, int e1, float px, float py, P &lo, P &hi, int &exact_o) {
+    const RoundSmem<P> &sm = round_smem<P>();
+    lo = hi = P(0);
+    if (right_of(sm.edge[e0], sm.vend[e0][0], sm.vend[e0][1], px, py, lo, hi, exact_o)) return e0;
+    if (right_of(sm.edge[e1], sm.vend[e1][0], sm.vend[e1][1], px, py, lo, hi, exact_o)) return e1;
+    return CLS_NONE;
+}
+
+// Initial split: the only edges of the CCW polygon A, [Bot,] B, [Top] a point
+// can be strictly right of.  Below the chord the point is right of A->Bot only
+// if x < Bot.x and of Bot->B only if x > Bot.x (Bot has the least y); above
+// it, of B->Top only if x > Top.x and of Top->A only if x < Top.x (Top has the
+// greatest y).  A chain without its middle vertex is the chord itself.  So the
+// lower-chain candidate is edge 0 or 1 and the upper-chain candidate edge iB
+// or iB + 1, chosen by exact comparisons of x; a point is right of at most one
+// of the two.
+__device__ __forceinline__ void split_edges(float px, bool hasBot, float botx, bool hasTop, float topx, int iB,
+                                            int &e0, int &e1) {
+    e0 = (hasBot & !(px < botx)) ? 1 : 0;
+    e1 = (hasTop & !(px > topx)) ? iB + 1 : iB;
+}
+
+// Warp totals of pass 1 -> sm.warpCnt, sm.maxLo; the packed slots -> sm.clsPack.
+template <typename P>
+__device__ __forceinline__ void pass1_commit(RoundSmem<P> &sm, unsigned cp0, unsigned cp1, unsigned cnt,
+                                             const unsigned (&mlo)[4]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    sm.clsPack[0][threadIdx.x] = cp0;
+    sm.clsPack[1][threadIdx.x] = cp1;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const unsigned wc = __reduce_add_sync(0xffffffffu, (cnt >> (8 * q)) & 0xffu);
+        const unsigned v = __reduce_max_sync(0xffffffffu, mlo[q]);
+        if (lane == 0) {
+            sm.warpCnt[w][q] = wc;
+            if (v) atomicMax(&sm.maxLo[q], v);
+        }
+    }
+}
+
+// Reserve the tile's output range in each of nslot children; warp offsets.
+template <typename P> __device__ __forceinline__ void tile_reserve(RoundSmem<P> &sm, int nslot, int *const (&cursor)[4]) {
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        int run = 0;
+        if (q < nslot) {
+            for (int w = 0; w < NWARP; w++) {
+                sm.warpOff[w][q] = run;
+                run += (int)sm.warpCnt[w][q];
+            }
+        }
+        sm.tot[q] = run;
+        sm.base[q] = run ? atomicAdd(cursor[q], run) : 0;
     }
     __syncthreads();
 }
 
+// Pass-2 rank of an item of slot c among its slot's points: the warp's running
+// rank plus the lane rank.
+__device__ __forceinline__ int slot_rank(int c, int (&wr)[4], unsigned lt) {
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const unsigned b = __ballot_sync(0xffffffffu, c == q);
+        rank = c == q ? wr[q] + __popc(b & lt) : rank;
+        wr[q] += __popc(b);
+    }
+    return rank;
+}
+
+// Candidate for the farthest point of slot c (pass 2): the key of its upper
+// bound reaches the slot's largest lower-bound key thr.
 template <typename P>
-__device__ __noinline__ bool phase_extremes(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC) {
+__device__ __forceinline__ void offer_candidate(RoundSmem<P> &sm, int c, unsigned thr, float px, float py, int idx) {
+    const DistIv<P> d = dist_interval(orient_approx(sm.edge[c], px, py));
+    if (pkey_up(d.hi) >= thr) {
+        const int j = atomicAdd(&sm.ncand, 1);
+        if (j < CAND_CAP) {
+            sm.cand[j] = mk_cand(px, py, idx);
+            sm.cslot[j] = (unsigned char)c;
+        }
+    }
+}
+
+// Slots in which this thread holds an item whose upper-bound key reaches the
+// slot's threshold (bit q for slot q).
+__device__ __forceinline__ unsigned candidate_slots(const unsigned (&mhi)[4], const unsigned (&thr)[4]) {
+    unsigned f = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) f |= (unsigned)((mhi[q] != 0u) & (mhi[q] >= thr[q])) << q;
+    return f;
+}
+
+template <typename T> __device__ __forceinline__ T sel4(int c, const T (&v)[4]) {
+    T r = v[0];
+    if (c == 1) r = v[1];
+    if (c == 2) r = v[2];
+    if (c == 3) r = v[3];
+    return r;
+}
+
+// Exact best candidate per slot -> sm.best.  Overflowing candidate lists
+// (massive exact ties) fall back to a full exact reduction over the tile.
+template <typename P, typename Fetch>
+__device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, int nItems, Fetch &&fetch,
+                                                   int &exact_c) {
+    __syncthreads();
+    const int nc = sm.ncand;
+    if (nc <= CAND_CAP) {
+        if (threadIdx.x < nslot) {
+            const int q = threadIdx.x;
+            Cand b = no_cand();
+            for (int j = 0; j < nc; j++)
+                if (sm.cslot[j] == q) cand_merge(b, sm.cand[j], q, sm, exact_c);
+            sm.best[q] = b;
+        }
+    } else {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        Cand b[4] = {no_cand(), no_cand(), no_cand(), no_cand()};
+        for (int i = threadIdx.x; i < nItems; i += NT) {
+            const int j = i / NT;
+            const int c = (int)((sm.clsPack[j >> 3][threadIdx.x] >> (4 * (j & 7))) & 15u);
+            if (c == CLS_NONE) continue;
+            float px, py;
+            int idx;
+            fetch(i, px, py, idx);
+            cand_merge(b[c], mk_cand(px, py, idx), c, sm, exact_c);
+        }
+        for (int q = 0; q < nslot; q++) {
+            for (int d = 16; d >= 1; d >>= 1) cand_merge(b[q], shfl_cand(b[q], lane ^ d), q, sm, exact_c);
+            if (lane == 0) sm.wbest[w][q] = b[q];
+        }
+        __syncthreads();
+        if (threadIdx.x < nslot) {
+            Cand r = no_cand();
+            for (int k = 0; k < NWARP; k++) cand_merge(r, sm.wbest[k][threadIdx.x], threadIdx.x, sm, exact_c);
+            sm.best[threadIdx.x] = r;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename P> __device__ __forceinline__ void tile_extremes_reset(RoundSmem<P> &sm) {
+    if (threadIdx.x == 0) {
+        sm.tk[0] = sm.tk[2] = 0xffffffffu;
+        sm.tk[1] = sm.tk[3] = 0u;
+    }
+}
+
+template <typename P> __device__ __forceinline__ void tile_reset(RoundSmem<P> &sm) {
+    if (threadIdx.x < 4) sm.maxLo[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) sm.ncand = 0;
+}
+
+// --------------------------------------------------------------------------
+// extremes (Sec. 4.2)
+// --------------------------------------------------------------------------
+// Coordinate extremes of the thread's items of a tile; a full tile needs no
+// per-item bound test.
+template <bool FULL>
+__device__ __forceinline__ void ext_pass_a(const float2 *xs, int dx, int nItems, float &mnx, float &mxx, float &mny,
+                                           float &mxy, bool &nan) {
+#pragma unroll
+    for (int j = 0; j < IPT; j++) {
+        const int i = j * NT + threadIdx.x;
+        if (FULL || i < nItems) {
+            const float2 v = xs[i + dx];
+            mnx = fminf(mnx, v.x);
+            mxx = fmaxf(mxx, v.x);
+            mny = fminf(mny, v.y);
+            mxy = fmaxf(mxy, v.y);
+            nan |= (v.x != v.x) | (v.y != v.y);
+        }
+    }
+}
+
+template <typename P>
+__device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long &gI,
+                                            unsigned long long &gC) {
+    RoundSmem<P> &sm = round_smem<P>();
     const long long T = __ldcg(&p.ctl->bigTiles), G = gridDim.x;
     const long long cb = (long long)blockIdx.x * T / G, ce = ((long long)blockIdx.x + 1) * T / G;
     const long long cnt = ce - cb;
@@ -829,7 +1031,8 @@ __device__ __noinline__ bool phase_extremes(const Params &p, RoundSmem<P> &sm, u
     q.kind = 0;
     q.S = q.cur = q.src = 0;
     q.L = 0;
-    pipe_start(p, sm, q, gI);
+    tile_extremes_reset(sm);
+    pipe_start<P>(p, q, gI);
     Ext acc = ext_empty();
     int accInst = -1, segTiles = 0;
     long long segFirst = 0;
@@ -839,47 +1042,95 @@ __device__ __noinline__ bool phase_extremes(const Params &p, RoundSmem<P> &sm, u
         const unsigned par = (unsigned)((gC / NS) & 1ull);
         gC++;
         if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
-            pipe_drain(p, sm, gI, gC);
+            pipe_drain<P>(p, gI, gC);
             return false;
         }
         QH_PROF(0);
         const TileRec &R = desc_of(sm, k);
         const int inst = R.inst;
         if (inst != accInst) {
-            if (accInst >= 0) ext_flush(p, sm, acc, accInst, segFirst, segTiles);
+            if (accInst >= 0) ext_flush<P>(p, acc, accInst, segFirst, segTiles);
             acc = ext_empty();
             accInst = inst;
             segFirst = R.t;
             segTiles = 0;
         }
-        const int nItems = R.nItems;
-        const long long base = R.lt * TILE;
-#pragma unroll
-        for (int kk = 0; kk < IPT; kk++) {
-            const int i = kk * NT + threadIdx.x;
-            if (i < nItems) {
-                const float2 q = fetch_xy(R, sm.stage[s], i, p.pts, true);
-                if (!isfinite(q.x) || !isfinite(q.y)) {
-                    acc.nonfinite = 1;
-                } else {
-                    const int id = (int)(base + i);
-                    if (lex_less(q.x, q.y, id, acc.a.x, acc.a.y, acc.a.idx)) acc.a = mk_cand(q.x, q.y, id);
-                    if (lex_greater(q.x, q.y, id, acc.b.x, acc.b.y, acc.b.idx)) acc.b = mk_cand(q.x, q.y, id);
-                    if (lex_less(q.y, q.x, id, acc.bot.y, acc.bot.x, acc.bot.idx)) acc.bot = mk_cand(q.x, q.y, id);
-                    if (lex_greater(q.y, q.x, id, acc.top.y, acc.top.x, acc.top.idx)) acc.top = mk_cand(q.x, q.y, id);
-                }
+        const int nItems = R.nItems, dx = R.g[0].dx;
+        const int base = (int)(R.lt * TILE);
+        const float2 *xs = sm.stage[s].xy;
+        // pass A: the tile's coordinate extremes (fminf/fmaxf skip NaN, flagged apart)
+        float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+        bool nan = false;
+        if (nItems == TILE)
+            ext_pass_a<true>(xs, dx, nItems, mnx, mxx, mny, mxy, nan);
+        else
+            ext_pass_a<false>(xs, dx, nItems, mnx, mxx, mny, mxy, nan);
+        if (nan) acc.nonfinite = 1;
+        {
+            QH_PROF(1);
+            const unsigned k0 = __reduce_min_sync(0xffffffffu, fkey(mnx));
+            const unsigned k1 = __reduce_max_sync(0xffffffffu, fkey(mxx));
+            const unsigned k2 = __reduce_min_sync(0xffffffffu, fkey(mny));
+            const unsigned k3 = __reduce_max_sync(0xffffffffu, fkey(mxy));
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&sm.tk[0], k0);
+                atomicMax(&sm.tk[1], k1);
+                atomicMin(&sm.tk[2], k2);
+                atomicMax(&sm.tk[3], k3);
             }
         }
-        segTiles++;
-        QH_PROF(1);
+        QH_PROF(7);
         __syncthreads();
         QH_PROF(2);
-        pipe_refill(p, sm, q, k, s, gI);
+        const float t0 = fkey_inv(sm.tk[0]), t1 = fkey_inv(sm.tk[1]), t2 = fkey_inv(sm.tk[2]),
+                    t3 = fkey_inv(sm.tk[3]);
+        if (!(fabsf(t0) <= FLT_MAX && fabsf(t1) <= FLT_MAX && fabsf(t2) <= FLT_MAX && fabsf(t3) <= FLT_MAX))
+            acc.nonfinite = 1;
+        // pass B: only points on a tile extreme can be a set extreme.  Hits are
+        // taken in increasing index order, so strict comparisons keep the lowest
+        // index among equal coordinates.
+        unsigned hm = 0u;
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int i = j * NT + threadIdx.x;
+            const float2 v = xs[i + dx];  // inside the stage for every j
+            const bool hit = (v.x == t0) | (v.x == t1) | (v.y == t2) | (v.y == t3);
+            hm |= (unsigned)(hit & (i < nItems)) << j;
+        }
+        while (hm) {
+            const int j = __ffs(hm) - 1;
+            hm &= hm - 1u;
+            const int i = j * NT + threadIdx.x;
+            const float2 v = xs[i + dx];
+            const int id = base + i;
+            if (acc.a.idx < 0 || v.x < acc.a.x || (v.x == acc.a.x && v.y < acc.a.y)) acc.a = mk_cand(v.x, v.y, id);
+            if (acc.b.idx < 0 || v.x > acc.b.x || (v.x == acc.b.x && v.y > acc.b.y)) acc.b = mk_cand(v.x, v.y, id);
+            if (acc.bot.idx < 0 || v.y < acc.bot.y || (v.y == acc.bot.y && v.x < acc.bot.x))
+                acc.bot = mk_cand(v.x, v.y, id);
+            if (acc.top.idx < 0 || v.y > acc.top.y || (v.y == acc.top.y && v.x > acc.top.x))
+                acc.top = mk_cand(v.x, v.y, id);
+        }
+        segTiles++;
         QH_PROF(3);
+        __syncthreads();
+        QH_PROF(4);
+        tile_extremes_reset(sm);
+        pipe_refill<P>(p, q, k, s, gI);
+        QH_PROF(5);
     }
-    if (accInst >= 0) ext_flush(p, sm, acc, accInst, segFirst, segTiles);
-    QH_PROF(4);
+#ifdef QH_PROFILE
+    const unsigned long long tLoop = global_ns();
+#endif
+    if (accInst >= 0) ext_flush<P>(p, acc, accInst, segFirst, segTiles);
+    QH_PROF(6);
     QH_PROF_FLUSH_AT(p.ctl, 8);
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) {  // latest loop end and flush end of any CTA, ns after the phase start
+        const unsigned long long t1 = __ldcg(&p.ctl->tphase[1]);
+        atomicMax(&p.ctl->prof[24], tLoop - t1);
+        atomicMax(&p.ctl->prof[25], global_ns() - t1);
+    }
+#endif
     return true;
 }
 
@@ -887,143 +1138,164 @@ __device__ __noinline__ bool phase_extremes(const Params &p, RoundSmem<P> &sm, u
 // round 0: the initial split
 // --------------------------------------------------------------------------
 template <typename P>
-__device__ __noinline__ bool phase_round0(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC,
-                             int &exact_o, int &exact_c, long long &survivors) {
-    const long long T = __ldcg(&p.ctl->bigTiles);
-    const long long first = blockIdx.x, step = gridDim.x;
-    const long long cnt = first < T ? (T - 1 - first) / step + 1 : 0;
+__device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &gI,
+                                          unsigned long long &gC, int &exact_o, int &exact_c, long long &survivors) {
+    RoundSmem<P> &sm = round_smem<P>();
+    const long long T = __ldcg(&p.ctl->bigTiles), G = gridDim.x;
+    const long long first = chunk_start(blockIdx.x, T, G);
+    const long long cnt = chunk_start(blockIdx.x + 1, T, G) - first;
     TileSeq q;
     q.first = first;
-    q.step = step;
+    q.step = 1;
     q.cnt = cnt;
     q.kind = 1;
     q.S = q.cur = q.src = 0;
     q.L = 0;
-    pipe_start(p, sm, q, gI);
+    tile_reset(sm);
+    pipe_start<P>(p, q, gI);
+    const unsigned lt = lanemask_lt();
+    const int w = threadIdx.x >> 5;
     QH_PROF_DECL;
+#ifdef QH_PROFILE
+    const unsigned long long gns0 = global_ns();
+    const long long clk0 = clock64();
+#endif
     for (long long kt = 0; kt < cnt; kt++) {
         const int s = (int)(gC % NS);
         const unsigned par = (unsigned)((gC / NS) & 1ull);
         gC++;
         QH_PROF(7);
         if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
-            pipe_drain(p, sm, gI, gC);
+            pipe_drain<P>(p, gI, gC);
             return false;
         }
         QH_PROF(0);
         const TileRec &R = desc_of(sm, kt);
-        const int K = R.K;
-        float x[IPT], y[IPT];
-        int idx[IPT], slot[IPT], rank[IPT];
-        P lo[IPT], hi[IPT];
-        const int nItems = R.nItems;
-        const long long base = R.lt * TILE;
-#pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int i = k * NT + threadIdx.x;
-            slot[k] = -1;
-            lo[k] = hi[k] = P(0);
-            x[k] = y[k] = 0.f;
-            idx[k] = (int)(base + i);
-            if (K > 0 && i < nItems) {
-                const float2 q = fetch_xy(R, sm.stage[s], i, p.pts, true);
-                x[k] = q.x;
-                y[k] = q.y;
-            }
+        const int K = R.K, nItems = R.nItems;
+        if (K == 0) {  // degenerate or rejected set: no segments
+            __syncthreads();
+            pipe_refill<P>(p, q, kt, s, gI);
+            continue;
         }
+        if (sm.run.node >= 0 && sm.run.node != R.inst) flush_run<P>(p, 1, T, exact_c);  // the previous set's run
+        if (sm.run.node < 0) run_start(sm.run, R.inst, K, R.t, 0, 0, R.tile0, R.tile0 + R.tiles - 1, 0);
         if (threadIdx.x < K) {
             const Cand u = R.poly[threadIdx.x], v = R.poly[(threadIdx.x + 1) % K];
             sm.edge[threadIdx.x] = make_edge<P>(u.x, u.y, v.x, v.y);
             sm.vend[threadIdx.x][0] = v.x;
             sm.vend[threadIdx.x][1] = v.y;
-        } else if (threadIdx.x == 32 && K > 0) {
-            const Cand u = R.poly[0], v = R.poly[R.iB];
-            sm.edge[4] = make_edge<P>(u.x, u.y, v.x, v.y);
-            sm.vend[4][0] = v.x;
-            sm.vend[4][1] = v.y;
         }
         __syncthreads();
-        pipe_refill(p, sm, q, kt, s, gI);
         QH_PROF(1);
-        if (K == 0) continue;  // degenerate or rejected set: no segments
-        const TileRec &C = R;
-        // A point lies strictly outside at most one edge of the initial polygon.
-        // Its side of the chord A->B tells which chain (A..B below, B..A above)
-        // can hold that edge; on the chord (or in the inner box) it is inside.
-        const int iB = C.iB, hasBox = C.hasBox;
-        const float bx0 = C.box[0], bx1 = C.box[1], by0 = C.box[2], by1 = C.box[3];
+        // pass 1: each point against its lower- and upper-chain candidate edge
+        const int iB = R.iB, dx = R.g[0].dx;
+        const bool hasBot = iB == 2, hasTop = K - iB == 2;
+        const float botx = R.poly[1].x, topx = R.poly[(iB + 1) & 3].x;
+        const float2 *xs = sm.stage[s].xy;
+        unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
+        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int i = k * NT + threadIdx.x;
-            if (i >= nItems) continue;
-            const float px = x[k], py = y[k];
-            if (hasBox && px >= bx0 && px <= bx1 && py >= by0 && py <= by1) continue;
-            const Edge<P> &ch = sm.edge[4];
-            const Approx<P> o = orient_approx(ch, px, py);
-            const int sg = orient_sign(ch, sm.vend[4][0], sm.vend[4][1], px, py, o, exact_o);
-            if (sg == 0) continue;
-            const int e0 = sg < 0 ? 0 : iB, e1 = sg < 0 ? iB : K;
-            if (e1 - e0 == 1) {  // the chain is the chord itself: A->B below, B->A above
-                const DistIv<P> d = dist_interval(o);
-                slot[k] = e0;
-                if (sg < 0) {
-                    lo[k] = d.lo;
-                    hi[k] = d.hi;
-                } else {  // distance right of B->A is +orient(A, B, P)
-                    lo[k] = -d.hi;
-                    hi[k] = -d.lo;
-                }
-                continue;
-            }
-            for (int e = e0; e < e1; e++) {
-                if (right_of(sm.edge[e], sm.vend[e][0], sm.vend[e][1], px, py, lo[k], hi[k], exact_o)) {
-                    slot[k] = e;
-                    break;
-                }
-            }
+        for (int j = 0; j < IPT; j++) {
+            const int i = j * NT + threadIdx.x;
+            const bool in = i < nItems;
+            const float2 v = xs[i + dx];  // inside the stage for every j; masked below
+            int e0, e1;
+            split_edges(v.x, hasBot, botx, hasTop, topx, iB, e0, e1);
+            P lo, hi;
+            bool unsure;
+            int c = classify_fast(sm, e0, e1, v.x, v.y, lo, hi, unsure);
+            c = in ? c : CLS_NONE;
+            um |= (unsigned)(unsure & in) << j;
+            note_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
+        while (um) {  // decisions the filter could not certify
+            const int j = __ffs(um) - 1;
+            um &= um - 1u;
+            const float2 v = xs[j * NT + threadIdx.x + dx];
+            int e0, e1;
+            split_edges(v.x, hasBot, botx, hasTop, topx, iB, e0, e1);
+            P lo, hi;
+            const int c = classify_exact<P>(e0, e1, v.x, v.y, lo, hi, exact_o);
+            renote_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
+        }
+        pass1_commit(sm, cp0, cp1, pc, mlo);
         QH_PROF(2);
-        unsigned tot[4];
-        tile_ranks(slot, rank, tot, sm);
+        Inst *W = &p.inst[R.inst];
+        int *const cursors[4] = {&W->chCount[0], &W->chCount[1], &W->chCount[2], &W->chCount[3]};
+        tile_reserve(sm, K, cursors);
         QH_PROF(3);
-        tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
-        QH_PROF(4);
-
-        const long long t = C.t;
-        Inst *W = &p.inst[C.inst];
-        if (threadIdx.x < K)  // reserve this tile's range in each initial segment
-            sm.base[threadIdx.x] = tot[threadIdx.x] ? atomicAdd(&W->chCount[threadIdx.x], (int)tot[threadIdx.x]) : 0;
-        if (threadIdx.x == 32) {
-            store_tile_bests(p, t, sm.best);
-            __threadfence();
-            sm.fflag[0] = atomicAdd(&W->done0, 1u) == (unsigned)C.tiles - 1u;
-        }
-        __syncthreads();
-        QH_PROF(5);
-        const long long off = C.setOff, n = C.setN;
+        // pass 2: write the survivors, then offer candidates
+        const long long off = R.setOff, n = R.setN;
+        const int idBase = (int)(R.lt * TILE);
+        int wr[4];
+        unsigned thr[4];
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int q = slot[k];
-            if (q < 0) continue;
-            const long long b = (q < 2 ? 0ll : p.ncap) + off;
-            const long long rr = (long long)sm.base[q] + rank[k];
-            const long long pos = (q & 1) ? b + n - 1 - rr : b + rr;
-            if (pos < b || pos >= b + n) {  // guard: never write outside the set's range
-                set_err(p.ctl, E_INTERNAL);
-                continue;
+        for (int qq = 0; qq < 4; qq++) {
+            wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
+            thr[qq] = sm.maxLo[qq];
+        }
+        float2 *oxy = p.xy[0];
+        int *oid = p.id[0];
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int i = j * NT + threadIdx.x;
+            const int c = item_cls(j, cp0, cp1);
+            const int rank = slot_rank(c, wr, lt);
+            const float2 v = xs[i + dx];
+            const long long b = (c < 2 ? 0ll : p.ncap) + off;
+            const long long pos = (c & 1) ? b + n - 1 - rank : b + rank;
+            const bool live = c != CLS_NONE;
+            bad |= live & (rank >= n);  // guard: never write outside the set's range
+            if (live & (rank < n)) {
+                __stcg(&oxy[pos], v);
+                __stcg(&oid[pos], idBase + i);
             }
-            __stcg(&p.xy[0][pos], make_float2(x[k], y[k]));
-            __stcg(&p.id[0][pos], idx[k]);
         }
-        if (sm.fflag[0]) {  // last tile of the set: farthest point of every initial segment
-            __threadfence();
-            merge_parent_bests(p, sm, C.tile0, C.tile0 + C.tiles - 1, 0, K, 0, exact_c);
-            if (threadIdx.x < K) stcg_cand(&W->chC[threadIdx.x], sm.fin[threadIdx.x]);
+        if (bad) set_err(p.ctl, E_INTERNAL);
+        if (const unsigned fl = candidate_slots(mhi, thr)) {
+            for (int j = 0; j < IPT; j++) {
+                const int c = item_cls(j, cp0, cp1);
+                if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
+                const int i = j * NT + threadIdx.x;
+                const float2 v = xs[i + dx];
+                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, idBase + i);
+            }
         }
-        if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
+        QH_PROF(4);
+        auto fetch = [&](int i, float &px, float &py, int &idx) {
+            const float2 v = xs[i + dx];
+            px = v.x;
+            py = v.y;
+            idx = idBase + i;
+        };
+        resolve_candidates(sm, K, nItems, fetch, exact_c);
+        if (threadIdx.x < K) cand_merge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
+        if (threadIdx.x == 0) {
+            sm.run.tiles++;
+            survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
+        }
+        QH_PROF(5);
+        tile_reset(sm);
+        pipe_refill<P>(p, q, kt, s, gI);
         QH_PROF(6);
     }
+    __syncthreads();
+    if (sm.run.node >= 0) flush_run<P>(p, 1, T, exact_c);
     QH_PROF_FLUSH(p.ctl);
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) {  // loop time in ns and in SM cycles (their ratio: the clock)
+        const unsigned long long dt = global_ns() - gns0;
+        atomicAdd(&p.ctl->prof[16], dt);
+        atomicAdd(&p.ctl->prof[17], (unsigned long long)(clock64() - clk0));
+        atomicMax(&p.ctl->prof[18], dt);
+        atomicMax(&p.ctl->prof[19], 1000000000ull - dt);
+        atomicMax(&p.ctl->prof[20], (dt << 16) | blockIdx.x);
+        atomicMax(&p.ctl->prof[21], (unsigned long long)cnt);
+        atomicMax(&p.ctl->prof[22], qh_prof_acc[2]);
+        atomicMax(&p.ctl->prof[23], qh_prof_acc[6]);
+    }
+#endif
     return true;
 }
 
@@ -1031,48 +1303,46 @@ __device__ __noinline__ bool phase_round0(const Params &p, RoundSmem<P> &sm, uns
 // round r >= 1
 // --------------------------------------------------------------------------
 template <typename P>
-__device__ __noinline__ bool phase_round(const Params &p, RoundSmem<P> &sm, unsigned long long &gI, unsigned long long &gC, int r,
-                            int S, long long L, int cur, int &exact_o, int &exact_c, long long &survivors) {
+__device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI,
+                                         unsigned long long &gC, int r, int S, long long L, int cur, int &exact_o,
+                                         int &exact_c, long long &survivors) {
+    RoundSmem<P> &sm = round_smem<P>();
     const int src = (r - 1) & 1, dst = r & 1;
-    const long long T = (L + TILE - 1) / TILE;
-    const long long first = blockIdx.x, step = gridDim.x;
-    const long long cnt = first < T ? (T - 1 - first) / step + 1 : 0;
+    const long long T = (L + TILE - 1) / TILE, G = gridDim.x;
+    const long long first = chunk_start(blockIdx.x, T, G);
+    const long long cnt = chunk_start(blockIdx.x + 1, T, G) - first;
     TileSeq q;
     q.first = first;
-    q.step = step;
+    q.step = 1;
     q.cnt = cnt;
     q.kind = 2;
     q.S = S;
     q.cur = cur;
     q.src = src;
     q.L = L;
-    pipe_start(p, sm, q, gI);
+    tile_reset(sm);
+    pipe_start<P>(p, q, gI);
+    const unsigned lt = lanemask_lt();
+    const int w = threadIdx.x >> 5;
     for (long long kt = 0; kt < cnt; kt++) {
         const int s = (int)(gC % NS);
         const unsigned par = (unsigned)((gC / NS) & 1ull);
         gC++;
         if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
-            pipe_drain(p, sm, gI, gC);
+            pipe_drain<P>(p, gI, gC);
             return false;
         }
         const TileRec &R = desc_of(sm, kt);
         const int valid = R.valid, np = R.np, nItems = R.nItems;
-        float x[IPT], y[IPT];
-        int idx[IPT], slot[IPT], rank[IPT];
-        P lo[IPT], hi[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int i = k * NT + threadIdx.x;
-            slot[k] = -1;
-            lo[k] = hi[k] = P(0);
-            x[k] = y[k] = 0.f;
-            idx[k] = -1;
-            if (valid && i < nItems) {
-                const float2 q = fetch_xy(R, sm.stage[s], i, p.xy[src], false);
-                x[k] = q.x;
-                y[k] = q.y;
-                idx[k] = fetch_id(R, sm.stage[s], i, p.id[src]);
-            }
+        if (!valid) {
+            __syncthreads();
+            pipe_refill<P>(p, q, kt, s, gI);
+            continue;
+        }
+        if (sm.run.node >= 0 && sm.run.node != R.node[0]) flush_run<P>(p, 2, T, exact_c);  // the previous segment
+        if (sm.run.node < 0) {
+            const long long vs = R.vstart[0], cn = R.count[0];
+            run_start(sm.run, R.node[0], 2, R.t, 0, 0, vs / TILE, (vs + cn - 1) / TILE, (vs % TILE) != 0 ? 2 : 0);
         }
         if (threadIdx.x < 2 * np) {
             const int part = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -1083,71 +1353,115 @@ __device__ __noinline__ bool phase_round(const Params &p, RoundSmem<P> &sm, unsi
             sm.vend[threadIdx.x][1] = v.y;
         }
         __syncthreads();
-        pipe_refill(p, sm, q, kt, s, gI);
-        if (!valid) continue;
-        const TileRec &C = R;
-        const long long vB = np == 2 ? (long long)C.g[1].vofs : (long long)TILE;
+        const int vB = np == 2 ? R.g[1].vofs : TILE;
+        const int dx0 = R.g[0].dx, dx1 = R.g[1].dx, di0 = R.g[0].di, di1 = R.g[1].di;
+        const float2 *xs = sm.stage[s].xy;
+        const int *is = sm.stage[s].id;
+        // pass 1: strictly right of h->c (first child) or of c->e (second child)
+        unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
+        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int i = k * NT + threadIdx.x;
-            if (i < nItems) {
-                const int s0 = (i >= vB) ? 2 : 0;
-                if (right_of(sm.edge[s0], sm.vend[s0][0], sm.vend[s0][1], x[k], y[k], lo[k], hi[k], exact_o))
-                    slot[k] = s0;
-                else if (right_of(sm.edge[s0 + 1], sm.vend[s0 + 1][0], sm.vend[s0 + 1][1], x[k], y[k], lo[k], hi[k],
-                                  exact_o))
-                    slot[k] = s0 + 1;
-            }
+        for (int j = 0; j < IPT; j++) {
+            const int i = j * NT + threadIdx.x;
+            const bool in = i < nItems;
+            const bool pb = i >= vB;
+            const float2 v = xs[i + (pb ? dx1 : dx0)];  // inside the stage for every j; masked below
+            P lo, hi;
+            bool unsure;
+            const int s0 = pb ? 2 : 0;
+            int c = classify_fast(sm, s0, s0 + 1, v.x, v.y, lo, hi, unsure);
+            c = in ? c : CLS_NONE;
+            um |= (unsigned)(unsure & in) << j;
+            note_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
-        unsigned tot[4];
-        tile_ranks(slot, rank, tot, sm);
-        tile_farthest(slot, x, y, idx, lo, hi, sm, exact_c);
-
-        const long long t = C.t;
-        if (threadIdx.x < 2 * np) {  // reserve this tile's range in each child
-            const int q = threadIdx.x;
-            Node *N = &p.nodes[C.node[q >> 1]];
-            sm.base[q] = tot[q] ? atomicAdd(&N->chCount[q & 1], (int)tot[q]) : 0;
+        while (um) {  // decisions the filter could not certify
+            const int j = __ffs(um) - 1;
+            um &= um - 1u;
+            const int i = j * NT + threadIdx.x;
+            const bool pb = i >= vB;
+            const float2 v = xs[i + (pb ? dx1 : dx0)];
+            P lo, hi;
+            const int s0 = pb ? 2 : 0;
+            const int c = classify_exact<P>(s0, s0 + 1, v.x, v.y, lo, hi, exact_o);
+            renote_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
-        if (threadIdx.x == 32) {
-            store_tile_bests(p, t, sm.best);
-            __threadfence();
-            for (int part = 0; part < 2; part++) {
-                int last = 0;
-                if (part < np) {
-                    const long long vs = C.vstart[part], cn = C.count[part];
-                    const unsigned nt = (unsigned)((vs + cn - 1) / TILE - vs / TILE + 1);
-                    last = atomicAdd(&p.nodes[C.node[part]].tdone, 1u) == nt - 1u;
-                }
-                sm.fflag[part] = last;
-            }
-        }
-        __syncthreads();
+        pass1_commit(sm, cp0, cp1, pc, mlo);
+        Node *NA = &p.nodes[R.node[0]];
+        Node *NB = &p.nodes[R.node[np == 2 ? 1 : 0]];
+        int *const cursors[4] = {&NA->chCount[0], &NA->chCount[1], &NB->chCount[0], &NB->chCount[1]};
+        tile_reserve(sm, 2 * np, cursors);
+        // pass 2: write the survivors, then offer candidates
+        const long long ps0 = R.pstart[0], ps1 = R.pstart[1];
+        const int cn0 = R.count[0], cn1 = R.count[1];
+        int wr[4];
+        unsigned thr[4];
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const int q = slot[k];
-            if (q < 0) continue;
-            const int part = q >> 1;
-            const long long ps = C.pstart[part], cn = C.count[part];
-            const long long rr = (long long)sm.base[q] + rank[k];
-            const long long pos = (q & 1) ? ps + cn - 1 - rr : ps + rr;
-            if (pos < ps || pos >= ps + cn || pos >= 2 * p.ncap) {
-                set_err(p.ctl, E_INTERNAL);  // guard: a child never leaves its parent's range
-                continue;
+        for (int qq = 0; qq < 4; qq++) {
+            wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
+            thr[qq] = sm.maxLo[qq];
+        }
+        float2 *oxy = p.xy[dst];
+        int *oid = p.id[dst];
+        const long long lim = 2 * p.ncap;
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int i = j * NT + threadIdx.x;
+            const int c = item_cls(j, cp0, cp1);
+            const int rank = slot_rank(c, wr, lt);
+            const bool pb = (c == 2) | (c == 3);  // second part (never for a discarded item)
+            const float2 v = xs[i + (pb ? dx1 : dx0)];
+            const int idx = is[i + (pb ? di1 : di0)];
+            const long long ps = pb ? ps1 : ps0;
+            const int cn = pb ? cn1 : cn0;
+            const long long pos = (c & 1) ? ps + cn - 1 - rank : ps + rank;
+            const bool live = c != CLS_NONE;
+            const bool okp = (rank < cn) & (pos < lim);
+            bad |= live & !okp;  // guard: a child never leaves its parent's range
+            if (live & okp) {
+                __stcg(&oxy[pos], v);
+                __stcg(&oid[pos], idx);
             }
-            __stcg(&p.xy[dst][pos], make_float2(x[k], y[k]));
-            __stcg(&p.id[dst][pos], idx[k]);
         }
-        for (int part = 0; part < np; part++) {
-            if (!sm.fflag[part]) continue;  // this tile closes the parent: farthest points of its children
-            __threadfence();
-            const long long vs = C.vstart[part], cn = C.count[part];
-            const long long ta = vs / TILE, tb = (vs + cn - 1) / TILE;
-            merge_parent_bests(p, sm, ta, tb, (vs % TILE) != 0 ? 2 : 0, 2, 2 * part, exact_c);
-            if (threadIdx.x < 2) stcg_cand(&p.nodes[C.node[part]].chC[threadIdx.x], sm.fin[threadIdx.x]);
+        if (bad) set_err(p.ctl, E_INTERNAL);
+        if (const unsigned fl = candidate_slots(mhi, thr)) {
+            for (int j = 0; j < IPT; j++) {
+                const int c = item_cls(j, cp0, cp1);
+                if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
+                const int i = j * NT + threadIdx.x;
+                const bool pb = (c == 2) | (c == 3);
+                const float2 v = xs[i + (pb ? dx1 : dx0)];
+                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, is[i + (pb ? di1 : di0)]);
+            }
         }
-        if (threadIdx.x == 0) survivors += (long long)tot[0] + tot[1] + tot[2] + tot[3];
+        auto fetch = [&](int i, float &px, float &py, int &idx) {
+            const bool pb = i >= vB;
+            const float2 v = xs[i + (pb ? dx1 : dx0)];
+            px = v.x;
+            py = v.y;
+            idx = is[i + (pb ? di1 : di0)];
+        };
+        resolve_candidates(sm, 2 * np, nItems, fetch, exact_c);
+        if (threadIdx.x < 2) cand_merge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
+        if (threadIdx.x == 0) {
+            sm.run.tiles++;
+            sm.run.edgeOff = 0;
+            survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
+        }
+        if (np == 2) {  // the first segment ends in this tile; the second starts here
+            __syncthreads();
+            flush_run<P>(p, 2, T, exact_c);
+            const long long vs = R.vstart[1], cn = R.count[1];
+            run_start(sm.run, R.node[1], 2, R.t, 2, 2, vs / TILE, (vs + cn - 1) / TILE, 2);
+            __syncthreads();
+            if (threadIdx.x < 2) sm.run.best[threadIdx.x] = sm.best[2 + threadIdx.x];
+            if (threadIdx.x == 0) sm.run.tiles = 1;
+        }
+        tile_reset(sm);
+        pipe_refill<P>(p, q, kt, s, gI);
     }
+    __syncthreads();
+    if (sm.run.node >= 0) flush_run<P>(p, 2, T, exact_c);
     return true;
 }
 
@@ -1157,7 +1471,8 @@ __device__ __noinline__ bool phase_round(const Params &p, RoundSmem<P> &sm, unsi
 // List the big nodes of [first, first + count) for the next round (exclusive
 // prefix of their sizes), queue the small ones for the block finisher.
 template <typename P>
-__device__ void build_biglist(const Params &p, RoundSmem<P> &sm, int first, int count, int dstBuf) {
+__device__ void build_biglist(const Params &p, int first, int count, int dstBuf) {
+    RoundSmem<P> &sm = round_smem<P>();
     long long *scr = sm.scanTmp;
     const int per = (count + NT - 1) / NT;
     const int b = min(count, threadIdx.x * per), e = min(count, b + per);
@@ -1208,7 +1523,8 @@ __device__ __forceinline__ int node_kind(int count, int cut) {
     return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
 }
 
-template <typename P> __device__ __noinline__ void build_level0(const Params &p, RoundSmem<P> &sm) {
+template <typename P> __device__ __noinline__ void build_level0(const Params &p) {
+    RoundSmem<P> &sm = round_smem<P>();
     long long *scr = sm.scanTmp;
     const int nBig = __ldcg(&p.ctl->nBig);
     long long carry = 0;
@@ -1259,10 +1575,11 @@ template <typename P> __device__ __noinline__ void build_level0(const Params &p,
         p.ctl->levelBase[0] = 0;
         p.ctl->levelBase[1] = (int)carry;
     }
-    build_biglist(p, sm, 0, (int)carry, 0);
+    build_biglist<P>(p, 0, (int)carry, 0);
 }
 
-template <typename P> __device__ __noinline__ void build_level(const Params &p, RoundSmem<P> &sm, int r) {
+template <typename P> __device__ __noinline__ void build_level(const Params &p, int r) {
+    RoundSmem<P> &sm = round_smem<P>();
     const int S = __ldcg(&p.ctl->S);
     const int cur = __ldcg(&p.ctl->cur);
     const int base = __ldcg(&p.ctl->nNodes);
@@ -1305,15 +1622,14 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
         p.ctl->levelBase[r + 1] = base + 2 * S;
         p.ctl->rounds = r;
     }
-    build_biglist(p, sm, base, 2 * S, cur ^ 1);
+    build_biglist<P>(p, base, 2 * S, cur ^ 1);
 }
 
 // --------------------------------------------------------------------------
 // the kernel
 // --------------------------------------------------------------------------
 template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(Params p) {
-    extern __shared__ __align__(128) unsigned char rounds_smem_raw[];
-    RoundSmem<P> &sm = *reinterpret_cast<RoundSmem<P> *>(rounds_smem_raw);
+    RoundSmem<P> &sm = round_smem<P>();
     unsigned phase = 0, donePhase = 0;
     int exact_o = 0, exact_c = 0;
     long long surv = 0;
@@ -1322,24 +1638,36 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++) mbar_init(&sm.mbar[s], 1u);
         fence_mbar_init();
+        sm.run.node = -1;
     }
     __syncthreads();
     stamp(p.ctl, 0);
-    if (blockIdx.x == 0) prep(p, sm);
+    if (blockIdx.x == 0) prep<P>(p);
     if (!grid_sync(p.ctl, phase)) goto out;
     stamp(p.ctl, 1);
 
-    phase_extremes(p, sm, gI, gC);
+    phase_extremes<P>(p, gI, gC);
     if (!grid_sync(p.ctl, phase)) goto out;
     stamp(p.ctl, 2);
 
-    phase_round0(p, sm, gI, gC, exact_o, exact_c, surv);
+    phase_round0<P>(p, gI, gC, exact_o, exact_c, surv);
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[26], global_ns() - __ldcg(&p.ctl->tphase[2]));
+#endif
     if (threadIdx.x == 0 && surv) {
         atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
         atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
     }
     surv = 0;
-    if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level0(p, sm);
+    if (last_cta(p.ctl, donePhase, &sm.kflag)) {
+#ifdef QH_PROFILE
+        const unsigned long long tb0 = global_ns();
+#endif
+        build_level0<P>(p);
+#ifdef QH_PROFILE
+        if (threadIdx.x == 0) p.ctl->prof[27] = global_ns() - tb0;
+#endif
+    }
     if (!grid_sync(p.ctl, phase)) goto out;
     stamp(p.ctl, 3);
 
@@ -1352,14 +1680,25 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
             if (blockIdx.x == 0 && threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
             break;
         }
-        phase_round(p, sm, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
+        phase_round<P>(p, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
+#ifdef QH_PROFILE
+        if (threadIdx.x == 0 && r <= 2) atomicMax(&p.ctl->prof[26 + 2 * r], global_ns() - __ldcg(&p.ctl->tphase[2 + r]));
+#endif
         if (threadIdx.x == 0 && surv) {
             atomicAdd((unsigned long long *)&p.ctl->live[min(r, MAX_GEN - 1)], (unsigned long long)surv);
             atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->gridRead += L;
         surv = 0;
-        if (last_cta(p.ctl, donePhase, &sm.kflag)) build_level(p, sm, r);
+        if (last_cta(p.ctl, donePhase, &sm.kflag)) {
+#ifdef QH_PROFILE
+            const unsigned long long tb0 = global_ns();
+#endif
+            build_level<P>(p, r);
+#ifdef QH_PROFILE
+            if (threadIdx.x == 0 && r <= 2) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
+#endif
+        }
         if (!grid_sync(p.ctl, phase)) goto out;
         stamp(p.ctl, 3 + r);
     }
