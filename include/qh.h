@@ -73,7 +73,7 @@ typedef struct {
     float phase_ms[5];          /* with timing on: grid rounds, finisher, emit, copy, total */
     float grid_phase_us[16];    /* inside the grid-wide kernel: set prep, extreme points, initial
                                    split, then grid-wide rounds 1.. (device clock) */
-    uint64_t section_cycles[32];/* per-tile section cycle sums of CTA thread 0; zero unless the
+    uint64_t section_cycles[48];/* per-tile section cycle sums of CTA thread 0; zero unless the
                                    library was built with -DQH_PROFILE */
     int64_t grid_points;        /* points of the sets tiled by the grid-wide kernel (read twice:
                                    extreme points and initial split) */

@@ -46,7 +46,7 @@ class _Stats(ctypes.Structure):
                 ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32),
                 ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
                 ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5),
-                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 32),
+                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 48),
                 ("grid_points", ctypes.c_int64), ("grid_read", ctypes.c_int64), ("grid_written", ctypes.c_int64),
                 ("small_points", ctypes.c_int64)]
 

@@ -387,7 +387,7 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
         if (c.live[g] > 0) last = g;
     }
     out->generations = last < 0 ? 1 : last + 2;
-    for (int k = 0; k < 32; k++) out->section_cycles[k] = c.prof[k];
+    for (int k = 0; k < 48; k++) out->section_cycles[k] = c.prof[k];
     out->exact_orient = (int64_t)c.exactOrient;
     out->grid_points = c.bigPoints;
     out->grid_read = c.gridRead;
@@ -455,3 +455,11 @@ qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_
 }
 
 }  // extern "C"
+
+#ifdef QH_PROFILE
+namespace qh {
+int prof_cta_copy(void *host, int n);
+}
+// Profiling builds only: per-CTA records of the initial split (8 x uint64 per CTA).
+extern "C" int qh_debug_prof_cta(void *host, int n) { return qh::prof_cta_copy(host, n); }
+#endif

@@ -106,7 +106,7 @@ struct Ctl {
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;
     unsigned long long tphase[MAX_LEVELS + 4];  // %globaltimer at the kernel start and after each grid barrier
-    unsigned long long prof[32];                // section cycle counters (profiling builds only)
+    unsigned long long prof[48];                // section cycle counters (profiling builds only)
 };
 
 struct Params {

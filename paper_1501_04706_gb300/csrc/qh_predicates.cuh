@@ -21,11 +21,19 @@
 // unusable and the point goes to the exact path.  In FP64 the products of
 // float differences neither underflow nor overflow.
 //
-// Exact path: every float x float product is exact in FP64; the sign of a sum of
-// such products is the sign of the top non-zero component of the nonoverlapping
-// expansion built with Knuth's TwoSum by Shewchuk's GROW-EXPANSION (Shewchuk,
-// "Adaptive precision floating-point arithmetic and fast robust geometric
-// predicates", 1997).  orient needs 6 products, the farthest-point comparison 8.
+// Exact path: the sign of a sum of products of floats is the sign of the top
+// non-zero component of the nonoverlapping expansion built with Knuth's TwoSum
+// by Shewchuk's GROW-EXPANSION (Shewchuk, "Adaptive precision floating-point
+// arithmetic and fast robust geometric predicates", 1997).  orient needs 6
+// products, the farthest-point comparison 8.  The expansion is built in FP32:
+// each product ab is the exact sum of p = fl(ab) and the FMA residue
+// fl(ab - p) when every factor is zero or has magnitude in [2^-51, 2^61]: then
+// ab is an integer multiple of 2^-148 and |ab - p| is at most 2^23 such units,
+// so the residue is representable, and |ab| < 2^122, so no partial sum of up to
+// 16 terms overflows (TwoSum is exact without overflow, subnormal sums
+// included).  Inputs outside that range take the same expansion in FP64, where
+// every float x float product is exact; FP64 runs at a small fraction of the
+// FP32 rate on the GPU, so it is kept for those inputs only.
 #pragma once
 
 #include <cfloat>
@@ -172,46 +180,116 @@ template <typename P> QH_HD Approx<P> orient_approx(const Edge<P> &e, float px, 
 }
 
 // --------------------------- exact fallback --------------------------------
-QH_HD void two_sum(double a, double b, double &s, double &e) {
+QH_HD float rfma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+
+template <typename T> QH_HD void two_sum(T a, T b, T &s, T &e) {
     s = radd(a, b);
-    double bb = rsub(s, a);
+    const T bb = rsub(s, a);
     e = radd(rsub(a, rsub(s, bb)), rsub(b, bb));
 }
 
-// Sign of t[0] + ... + t[n-1] (each an exact double), n <= 8.
-QH_HD int expansion_sign(const double *t, int n) {
-    double h[8];
-    int m = 0;
-    for (int i = 0; i < n; i++) {
-        double q = t[i];
-        for (int j = 0; j < m; j++) {
-            double s, err;
+// Sign of t[0] + ... + t[N-1] (each an exact value of type T) by
+// GROW-EXPANSION; kept as loops (the code is cold: its size costs more than
+// its speed).
+template <typename T, int N> QH_HD int expansion_sign(const T (&t)[N]) {
+    T h[N];
+#pragma unroll 1
+    for (int i = 0; i < N; i++) {
+        T q = t[i];
+#pragma unroll 1
+        for (int j = 0; j < i; j++) {
+            T s, err;
             two_sum(q, h[j], s, err);
             h[j] = err;
             q = s;
         }
-        h[m++] = q;
+        h[i] = q;
     }
-    for (int j = m - 1; j >= 0; j--)
-        if (h[j] != 0.0)
-            return h[j] > 0.0 ? 1 : -1;
+#pragma unroll 1
+    for (int j = N - 1; j >= 0; j--)  // the top non-zero component decides
+        if (h[j] != T(0)) return h[j] > T(0) ? 1 : -1;
     return 0;
+}
+
+QH_HD float fabs_f(float x) { return x < 0.f ? -x : x; }
+
+// Sign of p[0] + ... + p[N-1] (exact floats).  A VecSum pass (TwoSum along the
+// vector: p[i], p[i-1] <- sum, error) leaves the exact total unchanged and
+// moves its rounded value to p[N-1]; the sign is that of p[N-1] as soon as
+// |p[N-1]| exceeds the sum of the other magnitudes (accumulated rounding
+// upward, an upper bound), and 0 when that bound and p[N-1] are both zero.
+// Cases still open after a few passes take GROW-EXPANSION.
+template <int N> QH_HD int sum_sign_f32(float (&p)[N]) {
+#pragma unroll 1
+    for (int pass = 0; pass < 4; pass++) {
+#pragma unroll
+        for (int i = 1; i < N; i++) {
+            float s, e;
+            two_sum(p[i], p[i - 1], s, e);
+            p[i] = s;
+            p[i - 1] = e;
+        }
+        float rest = 0.f;
+#pragma unroll
+        for (int i = 0; i < N - 1; i++) rest = add_up(rest, fabs_f(p[i]));
+        const float top = p[N - 1];
+        if (fabs_f(top) > rest) return top > 0.f ? 1 : -1;
+        if (rest == 0.f) return 0;
+    }
+    return expansion_sign(p);
+}
+
+QH_HD bool f32_exact_range(float x) {
+    const float a = x < 0.f ? -x : x;
+    return a == 0.f || (a >= 0x1p-51f && a <= 0x1p61f);
 }
 
 QH_HD double xp(float a, float b) { return rmul(double(a), double(b)); }
 
+// sign(sum of s_k a_k b_k), s_k = +-1, exactly (FP32 expansion when in range).
+template <int N>
+QH_HD int product_sum_sign(const float (&a)[N], const float (&b)[N], const int (&sg)[N]) {
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < N; k++) in = in && f32_exact_range(a[k]) && f32_exact_range(b[k]);
+    if (in) {
+        float t[2 * N];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const float x = sg[k] > 0 ? a[k] : -a[k];
+            const float p = rmul(x, b[k]);
+            t[2 * k] = rfma(x, b[k], -p);
+            t[2 * k + 1] = p;
+        }
+        return sum_sign_f32(t);
+    }
+    double t[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) t[k] = sg[k] > 0 ? xp(a[k], b[k]) : -xp(a[k], b[k]);
+    return expansion_sign(t);
+}
+
 // orient(a,b,c) = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx, exactly.
 QH_HD_COLD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
-    double t[6] = {xp(bx, cy), -xp(bx, ay), -xp(ax, cy), -xp(by, cx), xp(by, ax), xp(ay, cx)};
-    return expansion_sign(t, 6);
+    const float fa[6] = {bx, bx, ax, by, by, ay};
+    const float fb[6] = {cy, ay, cy, cx, ax, cx};
+    const int sg[6] = {1, -1, -1, -1, 1, 1};
+    return product_sum_sign(fa, fb, sg);
 }
 
 // sign(dist(p) - dist(q)) for the chord u->v, dist(x) = -orient(u, v, x):
 //   -(vx-ux)(py-qy) + (vy-uy)(px-qx), expanded into eight exact products.
 QH_HD_COLD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, float py, float qx, float qy) {
-    double t[8] = {-xp(vx, py), xp(vx, qy), xp(ux, py), -xp(ux, qy),
-                   xp(vy, px), -xp(vy, qx), -xp(uy, px), xp(uy, qx)};
-    return expansion_sign(t, 8);
+    const float fa[8] = {vx, vx, ux, ux, vy, vy, uy, uy};
+    const float fb[8] = {py, qy, py, qy, px, qx, px, qx};
+    const int sg[8] = {-1, 1, 1, -1, 1, -1, -1, 1};
+    return product_sum_sign(fa, fb, sg);
 }
 
 // Decided sign of orient(u, v, p) given its filtered value; *exact_used counts fallbacks.

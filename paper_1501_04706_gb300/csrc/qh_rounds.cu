@@ -38,10 +38,17 @@
 
 namespace qh {
 
+#ifdef QH_PROFILE
+// Per-CTA records of the initial split (profiling builds only): loop ns, SM,
+// first tile, tiles, exact orientations, exact comparisons, pass-1 and
+// pass-2 cycles.
+__device__ unsigned long long qh_prof_cta[1024][8];
+#endif
+
 constexpr int NS = 2;          // pipeline stages per CTA
 constexpr int DB = 8;          // tile descriptors resolved per batch (one thread per tile)
 constexpr int CLS_NONE = 15;
-constexpr int CAND_CAP = 128;  // farthest-point candidates kept per tile before the fallback
+constexpr int CAND_CAP = 64;   // farthest-point candidates kept per tile before the fallback
 
 // Items of one segment inside a tile: physical range [q0, q0 + c) of the
 // source buffer, first tile-local item vofs.  The copies take the 16-byte
@@ -77,10 +84,17 @@ struct StageBuf {
     int id[TILE + STAGE_PAD];
 };
 
+// A farthest-point candidate with its distance interval beyond the slot's
+// edge, computed once: most comparisons are then two float comparisons.
+template <typename P> struct ICand {
+    Cand c;
+    P lo, hi;
+};
+
 // The CTA's running farthest-point candidates for the parent it is working on
 // (a run of consecutive tiles of one parent: a set in the initial split, a
 // segment in the rounds).
-struct RunAcc {
+template <typename P> struct RunAcc {
     int node;          // parent (set index in the initial split, node index in the rounds); -1: none
     int nslot;         // child slots of the parent
     int tiles;         // tiles merged into this run
@@ -91,12 +105,12 @@ struct RunAcc {
     int pad;
     long long first;   // tile holding this run's record
     long long ta, tb;  // first and last tile of the parent
-    Cand best[4];
+    ICand<P> best[4];
 };
 
 template <typename P> struct RoundSmem {
     unsigned long long mbar[NS];
-    RunAcc run;
+    RunAcc<P> run;
     TileRec desc[2][DB];  // descriptors of the CTA's tiles, double-buffered by batch
     // tile working set
     Edge<P> edge[4];   // per slot: the edge a point of the slot lies strictly right of
@@ -108,14 +122,15 @@ template <typename P> struct RoundSmem {
     unsigned maxLo[4];
     unsigned tk[4];  // extremes: keys of the tile's min x, max x, min y, max y
     int ncand;
-    Cand best[4];
+    ICand<P> best[4];
     Cand fin[4];
     int base[4];   // this tile's first output rank in each slot's child
     int fflag[2];  // this tile is the last of part A / part B's parent
     long long scanTmp[NWARP + 1];
     Ext wext[NWARP];
-    Cand wbest[NWARP][4];
-    Cand cand[CAND_CAP];
+    ICand<P> wbest[NWARP][4];
+    unsigned mthr[4];  // parent merge: largest lower-bound key per child
+    ICand<P> cand[CAND_CAP];
     unsigned char cslot[CAND_CAP];
     unsigned clsPack[2][NT];     // 4-bit slot of every item of the tile (CLS_NONE: discarded)
     alignas(128) StageBuf stage[NS];
@@ -294,21 +309,8 @@ __device__ __forceinline__ bool last_cta(Ctl *ctl, unsigned &donePhase, int *fla
 }
 
 // --------------------------------------------------------------------------
-// per-tile ranks and farthest points
+// farthest-point candidates
 // --------------------------------------------------------------------------
-// Merge candidate b into a for the chord of slot s (exact order).
-template <typename P>
-__device__ __forceinline__ void cand_merge(Cand &a, const Cand &b, int s, const RoundSmem<P> &sm, int &exact_c) {
-    if (b.idx < 0) return;
-    if (a.idx < 0) {
-        a = b;
-        return;
-    }
-    const Edge<P> &e = sm.edge[s];
-    const DistIv<P> da = dist_interval(orient_approx(e, a.x, a.y));
-    const DistIv<P> db = dist_interval(orient_approx(e, b.x, b.y));
-    if (farther(e, sm.vend[s][0], sm.vend[s][1], b.x, b.y, b.idx, db, a.x, a.y, a.idx, da, exact_c)) a = b;
-}
 
 // Classify a point against an edge: returns true when strictly right, with the
 // distance interval beyond the edge.
@@ -324,6 +326,45 @@ __device__ __forceinline__ bool right_of(const Edge<P> &e, float vx, float vy, f
         return true;
     }
     return false;
+}
+
+template <typename P> __device__ __forceinline__ ICand<P> no_icand() {
+    ICand<P> r;
+    r.c = no_cand();
+    r.lo = r.hi = P(0);
+    return r;
+}
+
+// Candidate c with its interval beyond the edge of slot s.
+template <typename P> __device__ __forceinline__ ICand<P> icand_of(const RoundSmem<P> &sm, int s, const Cand &c) {
+    ICand<P> r;
+    r.c = c;
+    const DistIv<P> d = dist_interval(orient_approx(sm.edge[s], c.x, c.y));
+    r.lo = d.lo;
+    r.hi = d.hi;
+    return r;
+}
+
+// a <- the farther of a and b beyond the edge of slot s (exact order).
+template <typename P>
+__device__ __forceinline__ void imerge(ICand<P> &a, const ICand<P> &b, int s, const RoundSmem<P> &sm, int &exact_c) {
+    if (b.c.idx < 0) return;
+    DistIv<P> da, db;
+    da.lo = a.lo;
+    da.hi = a.hi;
+    db.lo = b.lo;
+    db.hi = b.hi;
+    if (a.c.idx < 0 ||
+        farther(sm.edge[s], sm.vend[s][0], sm.vend[s][1], b.c.x, b.c.y, b.c.idx, db, a.c.x, a.c.y, a.c.idx, da, exact_c))
+        a = b;
+}
+
+template <typename P> __device__ __forceinline__ ICand<P> shfl_icand(const ICand<P> &a, int src) {
+    ICand<P> r;
+    r.c = shfl_cand(a.c, src);
+    r.lo = __shfl_sync(0xffffffffu, a.lo, src);
+    r.hi = __shfl_sync(0xffffffffu, a.hi, src);
+    return r;
 }
 
 // --------------------------------------------------------------------------
@@ -346,32 +387,92 @@ __device__ __forceinline__ long long chunk_of(long long t, long long T, long lon
 // Farthest point of every child of a parent spanning tiles [ta, tb] -> sm.fin.
 // The parent's runs start at ta (record slots slotBase0..) and at every chunk
 // start inside (ta, tb] (slots 0..), each holding the exact best of its tiles.
+// All records are read at once; only those whose upper bound reaches the
+// child's largest lower bound can be its farthest point, and only these are
+// compared (exactly) by one thread per child.
 template <typename P>
 __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long tb, int slotBase0, int nslot,
                                         int edgeOff, long long T, int &exact_c) {
     RoundSmem<P> &sm = round_smem<P>();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long G = gridDim.x;
-    Cand b[4] = {no_cand(), no_cand(), no_cand(), no_cand()};
-    if (threadIdx.x == 0)
-        for (int s = 0; s < nslot; s++) b[s] = ldcg_cand(&p.tbest[4 * ta + slotBase0 + s]);
     const long long c0 = chunk_of(ta, T, G), c1 = chunk_of(tb, T, G);
-    for (long long c = c0 + 1 + threadIdx.x; c <= c1; c += NT) {
-        const long long st = chunk_start(c, T, G);
-        if (st > ta && st < chunk_start(c + 1, T, G))  // a non-empty chunk starting inside the parent
-            for (int s = 0; s < nslot; s++)
-                cand_merge(b[s], ldcg_cand(&p.tbest[4 * st + s]), edgeOff + s, sm, exact_c);
-    }
-    for (int s = 0; s < nslot; s++) {
-        for (int d = 16; d >= 1; d >>= 1) cand_merge(b[s], shfl_cand(b[s], lane ^ d), edgeOff + s, sm, exact_c);
-        if (lane == 0) sm.wbest[w][s] = b[s];
+    const long long nrec = 1 + (c1 - c0);  // record 0 at ta, then the chunks c0 + 1 .. c1
+    constexpr int RPT = 2;                 // records per thread (grids of up to 2 * NT - 1 CTAs)
+    if (threadIdx.x < 4) sm.mthr[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        sm.ncand = 0;
+        if (nrec > (long long)RPT * NT) set_err(p.ctl, E_INTERNAL);
     }
     __syncthreads();
-    if (threadIdx.x < nslot) {
-        Cand r = no_cand();
-        for (int k = 0; k < NWARP; k++) cand_merge(r, sm.wbest[k][threadIdx.x], edgeOff + threadIdx.x, sm, exact_c);
-        sm.fin[threadIdx.x] = r;
+    ICand<P> rc[RPT][4];
+    unsigned mlo[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < RPT; k++) {
+        const long long r = threadIdx.x + (long long)k * NT;
+        long long tile = -1;
+        int base = 0;
+        if (r == 0) {
+            tile = ta;
+            base = slotBase0;
+        } else if (r < nrec) {
+            const long long st = chunk_start(c0 + r, T, G);
+            if (st > ta && st < chunk_start(c0 + r + 1, T, G)) tile = st;  // a non-empty chunk starting inside
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            rc[k][q] = no_icand<P>();
+            if (tile >= 0 && q < nslot) {
+                rc[k][q] = icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q]));
+                if (rc[k][q].c.idx >= 0) mlo[q] = max(mlo[q], max(pkey(rc[k][q].lo), 1u));
+            }
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const unsigned v = __reduce_max_sync(0xffffffffu, mlo[q]);
+        if (lane == 0 && v) atomicMax(&sm.mthr[q], v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RPT; k++)
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (rc[k][q].c.idx >= 0 && pkey_up(rc[k][q].hi) >= sm.mthr[q]) {
+                const int j = atomicAdd(&sm.ncand, 1);
+                if (j < CAND_CAP) {
+                    sm.cand[j] = rc[k][q];
+                    sm.cslot[j] = (unsigned char)q;
+                }
+            }
+    __syncthreads();
+    const int nc = sm.ncand;
+    if (nc <= CAND_CAP) {
+        if (threadIdx.x < nslot) {
+            const int q = threadIdx.x;
+            ICand<P> b = no_icand<P>();
+            for (int j = 0; j < nc; j++)
+                if (sm.cslot[j] == q) imerge(b, sm.cand[j], edgeOff + q, sm, exact_c);
+            sm.fin[q] = b.c;
+        }
+    } else {  // massive exact ties: reduce all records
+#pragma unroll 1
+        for (int q = 0; q < nslot; q++) {
+            ICand<P> b = rc[0][q];
+            imerge(b, rc[1][q], edgeOff + q, sm, exact_c);
+#pragma unroll 1
+            for (int d = 16; d >= 1; d >>= 1) imerge(b, shfl_icand(b, lane ^ d), edgeOff + q, sm, exact_c);
+            if (lane == 0) sm.wbest[w][q] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x < nslot) {
+            ICand<P> b = no_icand<P>();
+            for (int k = 0; k < NWARP; k++) imerge(b, sm.wbest[k][threadIdx.x], edgeOff + threadIdx.x, sm, exact_c);
+            sm.fin[threadIdx.x] = b.c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.ncand = 0;
     __syncthreads();
 }
 
@@ -382,10 +483,13 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
 template <typename P>
 __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, int &exact_c) {
     RoundSmem<P> &sm = round_smem<P>();
-    RunAcc &ra = sm.run;
+    RunAcc<P> &ra = sm.run;
     const int nslot = ra.nslot;
+#ifdef QH_PROFILE
+    const unsigned long long tf0 = global_ns();
+#endif
     if (threadIdx.x == 32) {
-        for (int s = 0; s < nslot; s++) stcg_cand(&p.tbest[4 * ra.first + ra.slotBase + s], ra.best[s]);
+        for (int s = 0; s < nslot; s++) stcg_cand(&p.tbest[4 * ra.first + ra.slotBase + s], ra.best[s].c);
         __threadfence();
         unsigned *cnt = kind == 1 ? &p.inst[ra.node].done0 : &p.nodes[ra.node].tdone;
         const unsigned old = atomicAdd(cnt, (unsigned)ra.tiles);
@@ -394,22 +498,32 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
     __syncthreads();
     if (sm.fflag[0]) {
         __threadfence();
+#ifdef QH_PROFILE
+        const unsigned long long tm0 = global_ns();
+#endif
         merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
+#ifdef QH_PROFILE
+        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[30], global_ns() - tm0);
+#endif
         if (threadIdx.x < nslot) {
             Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
             stcg_cand(dstC, sm.fin[threadIdx.x]);
         }
     }
     __syncthreads();
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[31], global_ns() - tf0);
+#endif
     if (threadIdx.x == 0) ra.node = -1;
     __syncthreads();
 }
 
 // Start a run of parent `node` at tile t (thread 0 sets the fields; the caller
 // synchronises before they are read).
-__device__ __forceinline__ void run_start(RunAcc &ra, int node, int nslot, long long t, int slotBase, int edgeOff,
+template <typename P>
+__device__ __forceinline__ void run_start(RunAcc<P> &ra, int node, int nslot, long long t, int slotBase, int edgeOff,
                                           long long ta, long long tb, int slotBase0) {
-    if (threadIdx.x < 4) ra.best[threadIdx.x] = no_cand();
+    if (threadIdx.x < 4) ra.best[threadIdx.x] = no_icand<P>();
     if (threadIdx.x == 0) {
         ra.node = node;
         ra.nslot = nslot;
@@ -769,14 +883,13 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
 // stores are coalesced) and collects the candidates whose upper bound reaches
 // the slot's largest lower bound.
 
-// Record the slot c (CLS_NONE: discarded) of item j (a compile-time index
-// after unrolling) with the keys of its distance bounds.
+// Record the slot c (CLS_NONE: discarded) of item j with the keys of its
+// distance bounds.
 __device__ __forceinline__ void note_item(int j, int c, unsigned klo, unsigned khi, unsigned &cp0, unsigned &cp1,
                                           unsigned &cnt, unsigned (&mlo)[4], unsigned (&mhi)[4]) {
-    if (j < 8)
-        cp0 |= (unsigned)c << (4 * j);
-    else
-        cp1 |= (unsigned)c << (4 * (j - 8));
+    const unsigned v = (unsigned)c << (4 * (j & 7));
+    cp0 |= j < 8 ? v : 0u;
+    cp1 |= j < 8 ? 0u : v;
     cnt += c < 4 ? 1u << (8 * c) : 0u;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -919,7 +1032,11 @@ __device__ __forceinline__ void offer_candidate(RoundSmem<P> &sm, int c, unsigne
     if (pkey_up(d.hi) >= thr) {
         const int j = atomicAdd(&sm.ncand, 1);
         if (j < CAND_CAP) {
-            sm.cand[j] = mk_cand(px, py, idx);
+            ICand<P> ic;
+            ic.c = mk_cand(px, py, idx);
+            ic.lo = d.lo;
+            ic.hi = d.hi;
+            sm.cand[j] = ic;
             sm.cslot[j] = (unsigned char)c;
         }
     }
@@ -952,14 +1069,14 @@ __device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, 
     if (nc <= CAND_CAP) {
         if (threadIdx.x < nslot) {
             const int q = threadIdx.x;
-            Cand b = no_cand();
+            ICand<P> b = no_icand<P>();
             for (int j = 0; j < nc; j++)
-                if (sm.cslot[j] == q) cand_merge(b, sm.cand[j], q, sm, exact_c);
+                if (sm.cslot[j] == q) imerge(b, sm.cand[j], q, sm, exact_c);
             sm.best[q] = b;
         }
     } else {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        Cand b[4] = {no_cand(), no_cand(), no_cand(), no_cand()};
+        ICand<P> b[4] = {no_icand<P>(), no_icand<P>(), no_icand<P>(), no_icand<P>()};
         for (int i = threadIdx.x; i < nItems; i += NT) {
             const int j = i / NT;
             const int c = (int)((sm.clsPack[j >> 3][threadIdx.x] >> (4 * (j & 7))) & 15u);
@@ -967,16 +1084,16 @@ __device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, 
             float px, py;
             int idx;
             fetch(i, px, py, idx);
-            cand_merge(b[c], mk_cand(px, py, idx), c, sm, exact_c);
+            imerge(b[c], icand_of(sm, c, mk_cand(px, py, idx)), c, sm, exact_c);
         }
         for (int q = 0; q < nslot; q++) {
-            for (int d = 16; d >= 1; d >>= 1) cand_merge(b[q], shfl_cand(b[q], lane ^ d), q, sm, exact_c);
+            for (int d = 16; d >= 1; d >>= 1) imerge(b[q], shfl_icand(b[q], lane ^ d), q, sm, exact_c);
             if (lane == 0) sm.wbest[w][q] = b[q];
         }
         __syncthreads();
         if (threadIdx.x < nslot) {
-            Cand r = no_cand();
-            for (int k = 0; k < NWARP; k++) cand_merge(r, sm.wbest[k][threadIdx.x], threadIdx.x, sm, exact_c);
+            ICand<P> r = no_icand<P>();
+            for (int k = 0; k < NWARP; k++) imerge(r, sm.wbest[k][threadIdx.x], threadIdx.x, sm, exact_c);
             sm.best[threadIdx.x] = r;
         }
     }
@@ -1003,7 +1120,7 @@ template <typename P> __device__ __forceinline__ void tile_reset(RoundSmem<P> &s
 template <bool FULL>
 __device__ __forceinline__ void ext_pass_a(const float2 *xs, int dx, int nItems, float &mnx, float &mxx, float &mny,
                                            float &mxy, bool &nan) {
-#pragma unroll
+#pragma unroll 4
     for (int j = 0; j < IPT; j++) {
         const int i = j * NT + threadIdx.x;
         if (FULL || i < nItems) {
@@ -1090,7 +1207,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
         // taken in increasing index order, so strict comparisons keep the lowest
         // index among equal coordinates.
         unsigned hm = 0u;
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const float2 v = xs[i + dx];  // inside the stage for every j
@@ -1194,7 +1311,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         const float2 *xs = sm.stage[s].xy;
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
         unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
@@ -1237,7 +1354,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         float2 *oxy = p.xy[0];
         int *oid = p.id[0];
         bool bad = false;
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
@@ -1270,7 +1387,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             idx = idBase + i;
         };
         resolve_candidates(sm, K, nItems, fetch, exact_c);
-        if (threadIdx.x < K) cand_merge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
+        if (threadIdx.x < K) imerge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
         if (threadIdx.x == 0) {
             sm.run.tiles++;
             survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
@@ -1294,6 +1411,19 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         atomicMax(&p.ctl->prof[21], (unsigned long long)cnt);
         atomicMax(&p.ctl->prof[22], qh_prof_acc[2]);
         atomicMax(&p.ctl->prof[23], qh_prof_acc[6]);
+        if (blockIdx.x < 1024) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            unsigned long long *rec = qh_prof_cta[blockIdx.x];
+            rec[0] = dt;
+            rec[1] = smid;
+            rec[2] = (unsigned long long)first;
+            rec[3] = (unsigned long long)cnt;
+            rec[4] = (unsigned long long)exact_o;
+            rec[5] = (unsigned long long)exact_c;
+            rec[6] = qh_prof_acc[2];
+            rec[7] = qh_prof_acc[4];
+        }
     }
 #endif
     return true;
@@ -1360,7 +1490,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         // pass 1: strictly right of h->c (first child) or of c->e (second child)
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
         unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
@@ -1404,7 +1534,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         int *oid = p.id[dst];
         const long long lim = 2 * p.ncap;
         bool bad = false;
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
@@ -1442,7 +1572,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             idx = is[i + (pb ? di1 : di0)];
         };
         resolve_candidates(sm, 2 * np, nItems, fetch, exact_c);
-        if (threadIdx.x < 2) cand_merge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
+        if (threadIdx.x < 2) imerge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
         if (threadIdx.x == 0) {
             sm.run.tiles++;
             sm.run.edgeOff = 0;
@@ -1682,7 +1812,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         }
         phase_round<P>(p, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
 #ifdef QH_PROFILE
-        if (threadIdx.x == 0 && r <= 2) atomicMax(&p.ctl->prof[26 + 2 * r], global_ns() - __ldcg(&p.ctl->tphase[2 + r]));
+        if (threadIdx.x == 0 && r <= 1) atomicMax(&p.ctl->prof[26 + 2 * r], global_ns() - __ldcg(&p.ctl->tphase[2 + r]));
 #endif
         if (threadIdx.x == 0 && surv) {
             atomicAdd((unsigned long long *)&p.ctl->live[min(r, MAX_GEN - 1)], (unsigned long long)surv);
@@ -1696,7 +1826,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
 #endif
             build_level<P>(p, r);
 #ifdef QH_PROFILE
-            if (threadIdx.x == 0 && r <= 2) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
+            if (threadIdx.x == 0 && r <= 1) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
 #endif
         }
         if (!grid_sync(p.ctl, phase)) goto out;
@@ -1737,6 +1867,15 @@ cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s) {
     return cudaLaunchCooperativeKernel((void *)rounds_kernel<float>, dim3(grid), dim3(NT), args,
                                        sizeof(RoundSmem<float>), s);
 }
+
+#ifdef QH_PROFILE
+int prof_cta_copy(void *host, int n) {
+    return cudaMemcpyFromSymbol(host, qh_prof_cta, sizeof(unsigned long long) * 8 * (size_t)min(n, 1024)) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
+#endif
 
 int rounds_max_ctas_per_sm(int prec) {
     int b = 0;

@@ -94,3 +94,59 @@ def test_loading_without_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(qh, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         qh.load()
+
+
+def _near_collinear(rng, scale, count):
+    """Triples on (or one ulp off) a float line y = fl(0.7 x), coordinates ~scale."""
+    out = []
+    for _ in range(count):
+        x = np.sort(rng.random(3)).astype(np.float32) * np.float32(scale)
+        y = (np.float32(0.7) * x).astype(np.float32)
+        k = rng.integers(0, 3)
+        if k:
+            y[1] = np.nextafter(y[1], np.float32((-1) ** k * np.inf))
+        out.append([x[0], y[0], x[2], y[2], x[1], y[1]])
+    return out
+
+
+def test_host_exact_paths_across_magnitudes(lib):
+    """The exact fallback runs in FP32 for factors in [2^-51, 2^61] (or zero) and
+    in FP64 outside; both sides of both limits, mixed scales and zeros agree
+    with rational arithmetic."""
+    import paper_1501_04706_gb300 as qh
+
+    rng = np.random.default_rng(11)
+    tri = []
+    for e in [-80, -60, -52, -51, -50, -20, 0, 20, 59, 60, 61, 62, 80]:
+        tri += _near_collinear(rng, 2.0 ** e, 150)
+        # exactly collinear: small integer multiples of one direction, scaled by 2^e
+        for _ in range(20):
+            d = rng.integers(-7, 8, size=2)
+            k = rng.integers(-9, 10, size=3)
+            tri.append([float(np.float32(2.0 ** e) * np.float32(v)) for i in k for v in (i * d[0], i * d[1])])
+    # mixed scales inside one triple, and exact zeros
+    for _ in range(600):
+        t = (rng.random(6) * 2 - 1).astype(np.float32)
+        t *= np.float32(2.0) ** rng.integers(-70, 70, size=6).astype(np.float32)
+        t[rng.random(6) < 0.2] = 0
+        tri.append(list(t))
+    tri = np.array(tri, dtype=np.float32)
+    assert np.isfinite(tri).all()
+    want = np.array([orient(t[0:2], t[2:4], t[4:6]) for t in tri])
+    for prec in (0, 1):
+        sign, cert = qh.check_orient_host(tri, prec)
+        assert np.array_equal(sign, want), prec
+    assert (want == 0).sum() > 100  # exact zeros were exercised
+
+    q = []
+    for e in [-80, -52, -51, -50, 0, 60, 61, 62, 80]:
+        for t in _near_collinear(rng, 2.0 ** e, 120):
+            # chord = first two points; p, q = third point and a one-ulp shift of it
+            p = np.array(t[4:6], dtype=np.float32)
+            qq = p.copy()
+            qq[rng.integers(0, 2)] = np.nextafter(qq[0], np.float32(np.inf)) if rng.random() < 0.5 else qq[1]
+            q.append(list(t[0:4]) + list(p) + list(qq))
+    q = np.array(q, dtype=np.float32)
+    got = qh.check_dist_host(q)
+    wantd = np.array([dist_sign(t[0:2], t[2:4], t[4:6], t[6:8]) for t in q])
+    assert np.array_equal(got, wantd)
