@@ -34,6 +34,15 @@ sys.path.insert(0, ROOT)
 METRIC = "2D hull Mpts/s (device-timed) and HBM GB/s vs 8 TB/s; filtered+batched vs plain FP64"
 WORKLOAD = "disk-20M: 20,000,000 points i.i.d. uniform in the unit disk (r = sqrt(U), angle = 2 pi U), seed 0"
 N_POINTS = 20_000_000
+
+
+def _set_points(n: int) -> None:
+    """Run the disk workload at n points (the benchmark line names the size)."""
+    global N_POINTS, WORKLOAD
+    if n != N_POINTS:
+        N_POINTS = int(n)
+        WORKLOAD = (f"disk-{n}: {n:,} points i.i.d. uniform in the unit disk (r = sqrt(U), angle = 2 pi U), "
+                    "seed 0 (profiling size, not the benchmark workload)")
 CPU_SAMPLE = 10_000_000
 
 
@@ -162,7 +171,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU-baseline legs")
+    ap.add_argument("--points", type=int, default=N_POINTS,
+                    help="points of the disk workload (default: the 20M-point benchmark; smaller sizes for profiling)")
     args = ap.parse_args()
+    _set_points(args.points)
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
