@@ -39,6 +39,8 @@
 namespace qh {
 
 #ifdef QH_PROFILE
+__device__ unsigned long long *qh_ctl_prof;
+__device__ __forceinline__ unsigned long long *round_ctl_prof() { return qh_ctl_prof; }
 // Per-CTA records of the initial split (profiling builds only): loop ns, SM,
 // first tile, tiles, exact orientations, exact comparisons, pass-1 and
 // pass-2 cycles.
@@ -46,9 +48,9 @@ __device__ unsigned long long qh_prof_cta[1024][8];
 #endif
 
 constexpr int NS = 2;          // pipeline stages per CTA
-constexpr int DB = 8;          // tile descriptors resolved per batch (one thread per tile)
+constexpr int DB = NT >= 256 ? 8 : 4;  // tile descriptors resolved per batch (one thread per tile)
 constexpr int CLS_NONE = 15;
-constexpr int CAND_CAP = 64;   // farthest-point candidates kept per tile before the fallback
+constexpr int CQ = NT >= 256 ? 16 : 12;  // farthest-point candidates kept per slot before the fallback
 
 // Items of one segment inside a tile: physical range [q0, q0 + c) of the
 // source buffer, first tile-local item vofs.  The copies take the 16-byte
@@ -121,7 +123,8 @@ template <typename P> struct RoundSmem {
     int tot[4];                  // points per slot in the tile
     unsigned maxLo[4];
     unsigned tk[4];  // extremes: keys of the tile's min x, max x, min y, max y
-    int ncand;
+    int nq[4];      // candidates per slot
+    int candOver;   // a slot's candidate list overflowed
     ICand<P> best[4];
     Cand fin[4];
     int base[4];   // this tile's first output rank in each slot's child
@@ -130,8 +133,7 @@ template <typename P> struct RoundSmem {
     Ext wext[NWARP];
     ICand<P> wbest[NWARP][4];
     unsigned mthr[4];  // parent merge: largest lower-bound key per child
-    ICand<P> cand[CAND_CAP];
-    unsigned char cslot[CAND_CAP];
+    ICand<P> candq[4][CQ];
     unsigned clsPack[2][NT];     // 4-bit slot of every item of the tile (CLS_NONE: discarded)
     alignas(128) StageBuf stage[NS];
 };
@@ -398,34 +400,30 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
     const long long G = gridDim.x;
     const long long c0 = chunk_of(ta, T, G), c1 = chunk_of(tb, T, G);
     const long long nrec = 1 + (c1 - c0);  // record 0 at ta, then the chunks c0 + 1 .. c1
-    constexpr int RPT = 2;                 // records per thread (grids of up to 2 * NT - 1 CTAs)
-    if (threadIdx.x < 4) sm.mthr[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
-        sm.ncand = 0;
-        if (nrec > (long long)RPT * NT) set_err(p.ctl, E_INTERNAL);
+    if (threadIdx.x < 4) {
+        sm.mthr[threadIdx.x] = 0u;
+        sm.nq[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
-    ICand<P> rc[RPT][4];
-    unsigned mlo[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int k = 0; k < RPT; k++) {
-        const long long r = threadIdx.x + (long long)k * NT;
-        long long tile = -1;
-        int base = 0;
+    // record r: its tile (-1: none) and record slot base
+    auto rec_tile = [&](long long r, int &base) -> long long {
+        base = 0;
         if (r == 0) {
-            tile = ta;
             base = slotBase0;
-        } else if (r < nrec) {
-            const long long st = chunk_start(c0 + r, T, G);
-            if (st > ta && st < chunk_start(c0 + r + 1, T, G)) tile = st;  // a non-empty chunk starting inside
+            return ta;
         }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            rc[k][q] = no_icand<P>();
-            if (tile >= 0 && q < nslot) {
-                rc[k][q] = icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q]));
-                if (rc[k][q].c.idx >= 0) mlo[q] = max(mlo[q], max(pkey(rc[k][q].lo), 1u));
-            }
+        const long long st = chunk_start(c0 + r, T, G);
+        return (st > ta && st < chunk_start(c0 + r + 1, T, G)) ? st : -1;  // a non-empty chunk starting inside
+    };
+    unsigned mlo[4] = {0u, 0u, 0u, 0u};
+    for (long long r = threadIdx.x; r < nrec; r += NT) {
+        int base;
+        const long long tile = rec_tile(r, base);
+        if (tile < 0) continue;
+        for (int q = 0; q < nslot; q++) {
+            const ICand<P> ic = icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q]));
+            if (ic.c.idx >= 0) mlo[q] = max(mlo[q], max(pkey(ic.lo), 1u));
         }
     }
 #pragma unroll
@@ -434,32 +432,38 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         if (lane == 0 && v) atomicMax(&sm.mthr[q], v);
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RPT; k++)
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (rc[k][q].c.idx >= 0 && pkey_up(rc[k][q].hi) >= sm.mthr[q]) {
-                const int j = atomicAdd(&sm.ncand, 1);
-                if (j < CAND_CAP) {
-                    sm.cand[j] = rc[k][q];
-                    sm.cslot[j] = (unsigned char)q;
-                }
+    for (long long r = threadIdx.x; r < nrec; r += NT) {
+        int base;
+        const long long tile = rec_tile(r, base);
+        if (tile < 0) continue;
+        for (int q = 0; q < nslot; q++) {
+            const ICand<P> ic = icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q]));
+            if (ic.c.idx >= 0 && pkey_up(ic.hi) >= sm.mthr[q]) {
+                const int j = atomicAdd(&sm.nq[q], 1);
+                if (j < CQ)
+                    sm.candq[q][j] = ic;
+                else
+                    sm.candOver = 1;
             }
+        }
+    }
     __syncthreads();
-    const int nc = sm.ncand;
-    if (nc <= CAND_CAP) {
+    if (!sm.candOver) {
         if (threadIdx.x < nslot) {
-            const int q = threadIdx.x;
+            const int q = threadIdx.x, n = sm.nq[q];
             ICand<P> b = no_icand<P>();
-            for (int j = 0; j < nc; j++)
-                if (sm.cslot[j] == q) imerge(b, sm.cand[j], edgeOff + q, sm, exact_c);
+            for (int j = 0; j < n; j++) imerge(b, sm.candq[q][j], edgeOff + q, sm, exact_c);
             sm.fin[q] = b.c;
         }
     } else {  // massive exact ties: reduce all records
 #pragma unroll 1
         for (int q = 0; q < nslot; q++) {
-            ICand<P> b = rc[0][q];
-            imerge(b, rc[1][q], edgeOff + q, sm, exact_c);
+            ICand<P> b = no_icand<P>();
+            for (long long r = threadIdx.x; r < nrec; r += NT) {
+                int base;
+                const long long tile = rec_tile(r, base);
+                if (tile >= 0) imerge(b, icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q])), edgeOff + q, sm, exact_c);
+            }
 #pragma unroll 1
             for (int d = 16; d >= 1; d >>= 1) imerge(b, shfl_icand(b, lane ^ d), edgeOff + q, sm, exact_c);
             if (lane == 0) sm.wbest[w][q] = b;
@@ -472,7 +476,8 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) sm.ncand = 0;
+    if (threadIdx.x < 4) sm.nq[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
 }
 
@@ -1030,14 +1035,15 @@ template <typename P>
 __device__ __forceinline__ void offer_candidate(RoundSmem<P> &sm, int c, unsigned thr, float px, float py, int idx) {
     const DistIv<P> d = dist_interval(orient_approx(sm.edge[c], px, py));
     if (pkey_up(d.hi) >= thr) {
-        const int j = atomicAdd(&sm.ncand, 1);
-        if (j < CAND_CAP) {
+        const int j = atomicAdd(&sm.nq[c], 1);
+        if (j < CQ) {
             ICand<P> ic;
             ic.c = mk_cand(px, py, idx);
             ic.lo = d.lo;
             ic.hi = d.hi;
-            sm.cand[j] = ic;
-            sm.cslot[j] = (unsigned char)c;
+            sm.candq[c][j] = ic;
+        } else {
+            sm.candOver = 1;
         }
     }
 }
@@ -1059,45 +1065,69 @@ template <typename T> __device__ __forceinline__ T sel4(int c, const T (&v)[4]) 
     return r;
 }
 
-// Exact best candidate per slot -> sm.best.  Overflowing candidate lists
-// (massive exact ties) fall back to a full exact reduction over the tile.
+// Exact best of every slot over all items of the tile -> sm.best (whole CTA).
+template <typename P, typename Fetch>
+__device__ __noinline__ void resolve_tile_exhaustive(RoundSmem<P> &sm, int nslot, int nItems, Fetch fetch,
+                                                     int &exact_c) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    ICand<P> b[4] = {no_icand<P>(), no_icand<P>(), no_icand<P>(), no_icand<P>()};
+    for (int i = threadIdx.x; i < nItems; i += NT) {
+        const int j = i / NT;
+        const int c = (int)((sm.clsPack[j >> 3][threadIdx.x] >> (4 * (j & 7))) & 15u);
+        if (c == CLS_NONE) continue;
+        float px, py;
+        int idx;
+        fetch(i, px, py, idx);
+        imerge(b[c], icand_of(sm, c, mk_cand(px, py, idx)), c, sm, exact_c);
+    }
+    for (int q = 0; q < nslot; q++) {
+        for (int d = 16; d >= 1; d >>= 1) imerge(b[q], shfl_icand(b[q], lane ^ d), q, sm, exact_c);
+        if (lane == 0) sm.wbest[w][q] = b[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < nslot) {
+        ICand<P> r = no_icand<P>();
+        for (int k = 0; k < NWARP; k++) imerge(r, sm.wbest[k][threadIdx.x], threadIdx.x, sm, exact_c);
+        sm.best[threadIdx.x] = r;
+    }
+}
+
+// Exact best candidate per slot -> sm.best[q], written by thread q (q < nslot),
+// which may use it without a further barrier.  Usually a slot has one
+// candidate; overflowing lists (massive exact ties) fall back to a full exact
+// reduction over the tile.
 template <typename P, typename Fetch>
 __device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, int nItems, Fetch &&fetch,
                                                    int &exact_c) {
     __syncthreads();
-    const int nc = sm.ncand;
-    if (nc <= CAND_CAP) {
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) {
+        const int nc = sm.nq[0] + sm.nq[1] + sm.nq[2] + sm.nq[3];
+        atomicAdd(&round_ctl_prof()[38], (unsigned long long)nc);
+        atomicAdd(&round_ctl_prof()[39], 1ull);
+        atomicMax(&round_ctl_prof()[40], (unsigned long long)nc);
+    }
+#endif
+    if (!sm.candOver) {
         if (threadIdx.x < nslot) {
-            const int q = threadIdx.x;
-            ICand<P> b = no_icand<P>();
-            for (int j = 0; j < nc; j++)
-                if (sm.cslot[j] == q) imerge(b, sm.cand[j], q, sm, exact_c);
+            const int q = threadIdx.x, n = sm.nq[q];
+            ICand<P> b = n ? sm.candq[q][0] : no_icand<P>();
+            for (int j = 1; j < n; j++) imerge(b, sm.candq[q][j], q, sm, exact_c);
             sm.best[q] = b;
         }
     } else {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        ICand<P> b[4] = {no_icand<P>(), no_icand<P>(), no_icand<P>(), no_icand<P>()};
-        for (int i = threadIdx.x; i < nItems; i += NT) {
-            const int j = i / NT;
-            const int c = (int)((sm.clsPack[j >> 3][threadIdx.x] >> (4 * (j & 7))) & 15u);
-            if (c == CLS_NONE) continue;
-            float px, py;
-            int idx;
-            fetch(i, px, py, idx);
-            imerge(b[c], icand_of(sm, c, mk_cand(px, py, idx)), c, sm, exact_c);
-        }
-        for (int q = 0; q < nslot; q++) {
-            for (int d = 16; d >= 1; d >>= 1) imerge(b[q], shfl_icand(b[q], lane ^ d), q, sm, exact_c);
-            if (lane == 0) sm.wbest[w][q] = b[q];
-        }
-        __syncthreads();
-        if (threadIdx.x < nslot) {
-            ICand<P> r = no_icand<P>();
-            for (int k = 0; k < NWARP; k++) imerge(r, sm.wbest[k][threadIdx.x], threadIdx.x, sm, exact_c);
-            sm.best[threadIdx.x] = r;
-        }
+        resolve_tile_exhaustive(sm, nslot, nItems, fetch, exact_c);
     }
-    __syncthreads();
+}
+
+// The per-tile lists, thresholds and overflow flag: reset after the barrier
+// that starts a tile (every read of the previous tile's values precedes it).
+template <typename P> __device__ __forceinline__ void tile_reset(RoundSmem<P> &sm) {
+    if (threadIdx.x < 4) {
+        sm.maxLo[threadIdx.x] = 0u;
+        sm.nq[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) sm.candOver = 0;
 }
 
 template <typename P> __device__ __forceinline__ void tile_extremes_reset(RoundSmem<P> &sm) {
@@ -1105,11 +1135,6 @@ template <typename P> __device__ __forceinline__ void tile_extremes_reset(RoundS
         sm.tk[0] = sm.tk[2] = 0xffffffffu;
         sm.tk[1] = sm.tk[3] = 0u;
     }
-}
-
-template <typename P> __device__ __forceinline__ void tile_reset(RoundSmem<P> &sm) {
-    if (threadIdx.x < 4) sm.maxLo[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) sm.ncand = 0;
 }
 
 // --------------------------------------------------------------------------
@@ -1287,6 +1312,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             return false;
         }
         QH_PROF(0);
+        tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int K = R.K, nItems = R.nItems;
         if (K == 0) {  // degenerate or rejected set: no segments
@@ -1303,7 +1329,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             sm.vend[threadIdx.x][1] = v.y;
         }
         __syncthreads();
-        QH_PROF(1);
+        QH_PROF(0);
         // pass 1: each point against its lower- and upper-chain candidate edge
         const int iB = R.iB, dx = R.g[0].dx;
         const bool hasBot = iB == 2, hasTop = K - iB == 2;
@@ -1380,6 +1406,10 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             }
         }
         QH_PROF(4);
+#ifdef QH_PROFILE
+        __syncthreads();  // profiling builds: separates the wait for the slowest warp
+        QH_PROF(5);
+#endif
         auto fetch = [&](int i, float &px, float &py, int &idx) {
             const float2 v = xs[i + dx];
             px = v.x;
@@ -1392,10 +1422,9 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             sm.run.tiles++;
             survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
         }
-        QH_PROF(5);
-        tile_reset(sm);
-        pipe_refill<P>(p, q, kt, s, gI);
         QH_PROF(6);
+        pipe_refill<P>(p, q, kt, s, gI);
+        QH_PROF(1);
     }
     __syncthreads();
     if (sm.run.node >= 0) flush_run<P>(p, 1, T, exact_c);
@@ -1462,6 +1491,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             pipe_drain<P>(p, gI, gC);
             return false;
         }
+        tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int valid = R.valid, np = R.np, nItems = R.nItems;
         if (!valid) {
@@ -1587,7 +1617,6 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             if (threadIdx.x < 2) sm.run.best[threadIdx.x] = sm.best[2 + threadIdx.x];
             if (threadIdx.x == 0) sm.run.tiles = 1;
         }
-        tile_reset(sm);
         pipe_refill<P>(p, q, kt, s, gI);
     }
     __syncthreads();
@@ -1760,6 +1789,9 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
 // --------------------------------------------------------------------------
 template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(Params p) {
     RoundSmem<P> &sm = round_smem<P>();
+#ifdef QH_PROFILE
+    if (blockIdx.x == 0 && threadIdx.x == 0) qh_ctl_prof = p.ctl->prof;
+#endif
     unsigned phase = 0, donePhase = 0;
     int exact_o = 0, exact_c = 0;
     long long surv = 0;
