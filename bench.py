@@ -171,6 +171,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU-baseline legs")
+    ap.add_argument("--study", choices=["modes", "sweep", "profile", "configs"], default=None,
+                    help="instead of the benchmark line: the five workloads in their stated forms (configs), "
+                         "quadrilateral vs chord initial split (modes), "
+                         "uniform-square size sweep (sweep) or per-sub-procedure times (profile), one JSON line each")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the disk workload (default: the 20M-point benchmark; smaller sizes for profiling)")
     args = ap.parse_args()
@@ -178,6 +182,8 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.study:
+        return run_study(args.study)
 
     import numpy as np
     import torch
@@ -316,16 +322,57 @@ def main():
         bc = torch.empty(len(boff) - 1, dtype=torch.int32, device=device)
         for _ in range(3):
             qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+        # one CUDA-graph-captured launch sequence for the whole batch
+        launch = "cuda graph"
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+            replay = graph.replay
+        except Exception as exc:  # capture refused: time the eager launches and say so
+            launch = f"eager (graph capture failed: {type(exc).__name__})"
+            torch.cuda.synchronize(device)
+            replay = lambda: qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+        replay()
+        torch.cuda.synchronize(device)
         eb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
         for a, b in eb:
             flush.fill_(1)
             a.record(stream)
-            qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+            replay()
             b.record(stream)
         torch.cuda.synchronize(device)
         msb = sum(a.elapsed_time(b) for a, b in eb) / len(eb)
+        # the same sets, one plain-FP64 call per set on one stream
+        nsets = len(boff) - 1
+        plan1 = qh.Plan(int(np.max(np.diff(boff))), 1, prec=qh.PREC_F64)
+        po = torch.empty(len(bp), dtype=torch.int32, device=device)
+        pc = torch.empty(nsets, dtype=torch.int32, device=device)
+
+        def per_instance():
+            for i in range(nsets):
+                a0, a1 = int(boff[i]), int(boff[i + 1])
+                qh.hull2d(d_bp[a0:a1], plan1, out=po[a0:a1], count=pc[i:i + 1], sync=False)
+
+        per_instance()
+        torch.cuda.synchronize(device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        a.record(stream)
+        per_instance()
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        msi = a.elapsed_time(b)
+        cb, cp = bc.cpu().numpy(), pc.cpu().numpy()
+        ob, op = bo.cpu().numpy(), po.cpu().numpy()
+        same = bool(np.array_equal(cb, cp)) and all(
+            np.array_equal(ob[boff[i]:boff[i] + cb[i]], op[boff[i]:boff[i] + cp[i]]) for i in range(nsets))
         extras["batched"] = {"value": len(bp) / (msb * 1e-3) / 1e6, "unit": "Mpts/s", "ms_per_step": msb,
-                             "sets": len(boff) - 1, "points": int(len(bp))}
+                             "sets": nsets, "points": int(len(bp)), "launch": launch,
+                             "per_instance_fp64": {"value": len(bp) / (msi * 1e-3) / 1e6, "unit": "Mpts/s",
+                                                   "ms": msi, "calls": nsets, "same_hulls_as_batched": same},
+                             "speedup_vs_per_instance_fp64": msi / msb}
+        plan1.close()
         planb.close()
 
     clk = clocks.summary()
@@ -347,6 +394,171 @@ def main():
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# Unit-square times of the paper's GPU pipeline on a Tesla K20c (Table 2), ms: (Mode 1, Mode 2).
+PAPER_SQUARE_MS = {100_000: (37.2, 61.7), 200_000: (36.4, 65.7), 500_000: (41.7, 69.2), 1_000_000: (44.8, 73.9),
+                   2_000_000: (55.9, 86.2), 5_000_000: (77.9, 118.5), 10_000_000: (124.7, 161.7),
+                   20_000_000: (206.0, 272.5)}
+
+
+def _time_hull(qh, torch, d_pts, plan, flush, reps: int = 5):
+    """Median device time (ms) of one hull with the L2 flushed before each, and the plan's stats."""
+    stream = torch.cuda.current_stream()
+    out = torch.empty(max(d_pts.shape[0], 1), dtype=torch.int32, device=d_pts.device)
+    cnt = torch.empty(1, dtype=torch.int32, device=d_pts.device)
+    for _ in range(2):
+        qh.hull2d(d_pts, plan, out=out, count=cnt, sync=False)
+    times = []
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        qh.hull2d(d_pts, plan, out=out, count=cnt, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2], plan.stats(), int(cnt.item())
+
+
+def run_study(study: str) -> None:
+    """Studies beside the benchmark (one JSON line per case):
+    modes   -- the quadrilateral initial split (the paper's Mode 1) against the chord split (Mode 2) on the
+               single-set workloads: device time and live points per generation;
+    sweep   -- uniform unit square from 100K to 20M points in both modes, with the paper's K20c times (Table 2)
+               as context;
+    profile -- the time of each sub-procedure (set prep, extreme points, initial split, every grid round,
+               block finisher, output) on every workload, from the device clock and CUDA events."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as entry
+    import synth
+
+    entry.build()
+    import paper_1501_04706_gb300 as qh
+
+    qh.load()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    modes = [("quadrilateral", qh.MODE_QUAD), ("chord", qh.MODE_CHORD)]
+    if study == "configs":
+        return _study_configs(qh, torch, np, synth, device, flush)
+    if study in ("modes", "profile"):
+        cases = [("square-100K", synth.square()), ("disk-20M", synth.disk()), ("circle-20M", synth.circle()),
+                 ("degenerate-16M", synth.degenerate())]
+        for name, pts in cases:
+            d_pts = torch.from_numpy(pts).to(device)
+            plan = qh.Plan(len(pts), 1)
+            for mname, mode in (modes if study == "modes" else modes[:1]):
+                plan.set_flags(mode, qh.PREC_F32)
+                plan.set_tuning(4096, timing=study == "profile")
+                ms, st, h = _time_hull(qh, torch, d_pts, plan, flush)
+                line = {"study": study, "workload": name, "mode": mname, "n": len(pts), "hull_vertices": h,
+                        "ms": ms, "mpts_per_s": len(pts) / (ms * 1e-3) / 1e6}
+                if study == "modes":
+                    live = [int(v) for v in st["live"]]
+                    while live and live[-1] == 0:
+                        live.pop()
+                    line.update({"live_per_generation": live, "grid_rounds": st["global_rounds"],
+                                 "generations": st["generations"], "exact_orient": st["exact_orient"],
+                                 "exact_compare": st["exact_compare"]})
+                else:
+                    g = [round(v, 1) for v in st["grid_phase_us"] if v > 0]
+                    ph = st["phase_ms"]
+                    line.update({"us": {"set_prep": g[0] if g else None, "extreme_points": g[1] if len(g) > 1 else None,
+                                        "initial_split": g[2] if len(g) > 2 else None, "grid_rounds": g[3:],
+                                        "block_finisher": round(ph[1] * 1e3, 1),
+                                        "output_emit_copy": round((ph[2] + ph[3]) * 1e3, 1)},
+                                 "timing_note": "per-phase events and device-clock stamps on; ms is the timed hull"})
+                print(json.dumps(line), flush=True)
+            plan.close()
+            del d_pts
+    else:
+        for n in sorted(PAPER_SQUARE_MS):
+            pts = synth.square(n)
+            d_pts = torch.from_numpy(pts).to(device)
+            plan = qh.Plan(n, 1)
+            for k, (mname, mode) in enumerate(modes):
+                plan.set_flags(mode, qh.PREC_F32)
+                ms, st, h = _time_hull(qh, torch, d_pts, plan, flush)
+                print(json.dumps({"study": "sweep", "workload": f"square-{n}", "mode": mname, "n": n,
+                                  "hull_vertices": h, "ms": ms, "mpts_per_s": n / (ms * 1e-3) / 1e6,
+                                  "paper_k20c_ms": PAPER_SQUARE_MS[n][k],
+                                  "paper_note": "Table 2, Tesla K20c, timed region unstated: context only"}),
+                      flush=True)
+            plan.close()
+            del d_pts
+
+
+def _alg_bytes(n: int, live, h: int) -> int:
+    """Algorithmic bytes of the path: 8n (extreme points) + 8n (initial split read) + 12 L0 (its writes)
+    + sum over later generations of 12 (L_{r-1} + L_r) (read and write) + 4h (output)."""
+    live = [int(v) for v in live]
+    b = 16 * n + 4 * h + (12 * live[0] if live else 0)
+    for r in range(1, len(live)):
+        b += 12 * (live[r - 1] + live[r])
+    return b
+
+
+def _study_configs(qh, torch, np, synth, device, flush):
+    """The five workloads in the forms they are stated in: device time, Mpts/s, algorithmic GB/s against
+    8 TB/s nominal and the measured copy peak, exact-fallback rates, parity with the oracle."""
+    import oracle
+
+    peak, _ = _peaks()
+    runs = [("1: square-100K", synth.square, [("plain FP64", qh.PREC_F64)]),
+            ("2: disk-20M", synth.disk, [("plain FP64", qh.PREC_F64), ("FP32 filtered", qh.PREC_F32)]),
+            ("3: circle-20M", synth.circle, [("FP32 filtered", qh.PREC_F32)]),
+            ("4: degenerate-16M", synth.degenerate, [("FP32 filtered", qh.PREC_F32)])]
+    for name, gen, forms in runs:
+        pts = gen()
+        want = oracle.hull2d(pts)
+        d_pts = torch.from_numpy(pts).to(device)
+        plan = qh.Plan(len(pts), 1)
+        for form, prec in forms:
+            plan.set_flags(qh.MODE_QUAD, prec)
+            ms, st, h = _time_hull(qh, torch, d_pts, plan, flush, reps=9)
+            got = qh.hull2d(d_pts, plan).cpu().numpy()
+            ab = _alg_bytes(len(pts), st["live"], h)
+            gbs = ab / (ms * 1e-3) / 1e9
+            print(json.dumps({"study": "configs", "config": name, "form": form, "n": len(pts), "hull_vertices": h,
+                              "ms": ms, "mpts_per_s": len(pts) / (ms * 1e-3) / 1e6, "algorithmic_gb": ab / 1e9,
+                              "algorithmic_gbs": gbs, "frac_of_8tbs": gbs / 8000.0, "frac_of_measured_copy": gbs / peak,
+                              "exact_orient_per_point": st["exact_orient"] / len(pts),
+                              "exact_compare": st["exact_compare"], "parity": bool(np.array_equal(got, want))}),
+                  flush=True)
+        plan.close()
+        del d_pts
+    bp, boff = synth.batched()
+    d_bp = torch.from_numpy(bp).to(device)
+    d_off = torch.from_numpy(boff).to(device)
+    planb = qh.Plan(len(bp), len(boff) - 1)
+    bo = torch.empty(len(bp), dtype=torch.int32, device=device)
+    bc = torch.empty(len(boff) - 1, dtype=torch.int32, device=device)
+    qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
+    times = []
+    for _ in range(9):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    ms = times[len(times) // 2]
+    st = planb.stats()
+    print(json.dumps({"study": "configs", "config": "5: batched 4096 sets", "form": "FP32 filtered, one CUDA graph",
+                      "n": int(len(bp)), "ms": ms, "mpts_per_s": len(bp) / (ms * 1e-3) / 1e6,
+                      "exact_orient_per_point": st["exact_orient"] / len(bp), "exact_compare": st["exact_compare"],
+                      "parity": "per set in tests/test_gpu_parity.py (batched == oracle per set)"}), flush=True)
+    planb.close()
 
 
 def _kernel_rev() -> str:
