@@ -320,6 +320,7 @@ def main():
         planb = qh.Plan(len(bp), len(boff) - 1)
         bo = torch.empty(len(bp), dtype=torch.int32, device=device)
         bc = torch.empty(len(boff) - 1, dtype=torch.int32, device=device)
+        tuned = planb.autotune(d_bp, d_off, out=bo, counts=bc, reps=2)  # block size, CTAs per SM, cutover
         for _ in range(3):
             qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
         # one CUDA-graph-captured launch sequence for the whole batch
@@ -368,7 +369,7 @@ def main():
         same = bool(np.array_equal(cb, cp)) and all(
             np.array_equal(ob[boff[i]:boff[i] + cb[i]], op[boff[i]:boff[i] + cp[i]]) for i in range(nsets))
         extras["batched"] = {"value": len(bp) / (msb * 1e-3) / 1e6, "unit": "Mpts/s", "ms_per_step": msb,
-                             "sets": nsets, "points": int(len(bp)), "launch": launch,
+                             "sets": nsets, "points": int(len(bp)), "launch": launch, "autotuned": tuned,
                              "per_instance_fp64": {"value": len(bp) / (msi * 1e-3) / 1e6, "unit": "Mpts/s",
                                                    "ms": msi, "calls": nsets, "same_hulls_as_batched": same},
                              "speedup_vs_per_instance_fp64": msi / msb}
@@ -538,6 +539,7 @@ def _study_configs(qh, torch, np, synth, device, flush):
     planb = qh.Plan(len(bp), len(boff) - 1)
     bo = torch.empty(len(bp), dtype=torch.int32, device=device)
     bc = torch.empty(len(boff) - 1, dtype=torch.int32, device=device)
+    tuned = planb.autotune(d_bp, d_off, out=bo, counts=bc, reps=2)
     qh.hull2d_batched(d_bp, d_off, planb, out=bo, counts=bc)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
@@ -555,6 +557,7 @@ def _study_configs(qh, torch, np, synth, device, flush):
     ms = times[len(times) // 2]
     st = planb.stats()
     print(json.dumps({"study": "configs", "config": "5: batched 4096 sets", "form": "FP32 filtered, one CUDA graph",
+                      "autotuned": tuned,
                       "n": int(len(bp)), "ms": ms, "mpts_per_s": len(bp) / (ms * 1e-3) / 1e6,
                       "exact_orient_per_point": st["exact_orient"] / len(bp), "exact_compare": st["exact_compare"],
                       "parity": "per set in tests/test_gpu_parity.py (batched == oracle per set)"}), flush=True)

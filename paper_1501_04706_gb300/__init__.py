@@ -67,6 +67,10 @@ def load() -> ctypes.CDLL:
     lib.qh_plan_destroy.argtypes = [vp]
     lib.qh_plan_set_flags.argtypes = [vp, u32]
     lib.qh_plan_set_tuning.argtypes = [vp, i32, i32, i32]
+    lib.qh_plan_set_block.argtypes = [vp, i32]
+    lib.qh_plan_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32)]
+    lib.qh_plan_autotune.argtypes = [vp, vp, vp, i32, i64, vp, vp, i32, vp]
     lib.qh_hull2d_p.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.qh_hull2d.argtypes = [vp, i64, vp, vp, vp]
     lib.qh_hull2d_batched.argtypes = [vp, vp, vp, i32, vp, vp, vp]
@@ -79,7 +83,8 @@ def load() -> ctypes.CDLL:
     lib.qh_check_orient_device.argtypes = [vp, i64, i32, vp, vp, vp]
     lib.qh_check_dist_host.argtypes = [vp, i64, vp]
     lib.qh_check_dist_device.argtypes = [vp, i64, vp, vp]
-    for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_hull2d_p",
+    for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_plan_set_block",
+              "qh_plan_get_tuning", "qh_plan_autotune", "qh_hull2d_p",
               "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_plan_get_stats", "qh_check_orient_host",
               "qh_check_orient_device", "qh_check_dist_host", "qh_check_dist_device"):
         getattr(lib, f).restype = ctypes.c_int
@@ -126,6 +131,35 @@ class Plan:
     def set_tuning(self, cutover: int = 4096, timing: bool = False, ctas_per_sm: int = 0) -> None:
         _check(load().qh_plan_set_tuning(self.handle, int(cutover), int(bool(timing)), int(ctas_per_sm)),
                "qh_plan_set_tuning")
+
+    def set_block(self, threads: int) -> None:
+        """Block size of the grid-wide kernel: 256 or 128 threads (16 points per thread)."""
+        _check(load().qh_plan_set_block(self.handle, int(threads)), "qh_plan_set_block")
+
+    def tuning(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(load().qh_plan_get_tuning(self.handle, *[ctypes.byref(x) for x in v]), "qh_plan_get_tuning")
+        return {"threads_per_block": v[0].value, "items_per_thread": v[1].value, "cutover": v[2].value,
+                "grid_ctas_per_sm": v[3].value}
+
+    def autotune(self, points, offsets=None, out=None, counts=None, reps: int = 3) -> dict:
+        """Time every candidate setting on this input, keep the fastest; returns the chosen tuning."""
+        import torch
+
+        pts = _points_tensor(points)
+        dev = pts.device
+        if offsets is None:
+            num_sets, off_ptr = 1, None
+        else:
+            off = offsets.to(device=dev, dtype=torch.int64).contiguous()
+            num_sets, off_ptr = off.shape[0] - 1, off.data_ptr()
+        if out is None:
+            out = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=dev)
+        if counts is None:
+            counts = torch.empty(max(num_sets, 1), dtype=torch.int32, device=dev)
+        _check(load().qh_plan_autotune(self.handle, pts.data_ptr(), off_ptr, num_sets, pts.shape[0], out.data_ptr(),
+                                       counts.data_ptr(), int(reps), _stream(dev)), "qh_plan_autotune")
+        return self.tuning()
 
     def stats(self) -> dict:
         s = _Stats()

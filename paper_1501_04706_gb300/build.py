@@ -18,6 +18,13 @@ LIB_PATH = os.path.join(OUT_DIR, "libqh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu", "qh_noalloc.cu"]
+# Translation units: (source, object name, flags).  The grid-wide kernel is compiled once per variant
+# (threads per CTA, CTAs per SM), each in its own namespace; the plan picks one at run time.
+UNITS = [("qh_rounds.cu", "qh_rounds_v256", ["-DQH_NT=256", "-DQH_MINB=2", "-DQH_VARIANT_NS=v256"]),
+         ("qh_rounds.cu", "qh_rounds_v128", ["-DQH_NT=128", "-DQH_MINB=4", "-DQH_VARIANT_NS=v128"]),
+         ("qh_finish.cu", "qh_finish", []),
+         ("qh_api.cu", "qh_api", []),
+         ("qh_noalloc.cu", "qh_noalloc", [])]
 HEADERS = ["qh_internal.cuh", "qh_predicates.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -53,9 +60,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     nvcc = _nvcc()
     extra = list(extra or [])
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + tag + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra]
+    def compile_one(unit) -> str:
+        src, name, flags = unit
+        obj = os.path.join(OUT_DIR, name + tag + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *flags, *extra]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         cmd += ["-c", os.path.join(CSRC, src), "-o", obj]
@@ -66,8 +74,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=OUT_DIR)
     os.close(fd)
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]

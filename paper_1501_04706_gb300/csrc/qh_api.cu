@@ -17,7 +17,8 @@ struct qh_plan_s {
     long long ncap = 0;
     int maxSets = 0;
     unsigned flags = 0;
-    int cut = TILE;
+    int cut = 16 * 256;  // small-segment cutover (>= the tile of the variant)
+    int variant = 0;     // grid-wide kernel variant (rounds_variant)
     int timing = 0;
     int ctasPerSm = 0;
     int numSMs = 0;
@@ -106,15 +107,15 @@ qh_status plan_alloc(qh_plan p) {
     QH_ALLOC(p->id[0], 2 * N);
     QH_ALLOC(p->id[1], 2 * N);
     QH_ALLOC(p->vscratch, 2 * N);
-    p->maxTiles = N / TILE + p->maxSets + 16;
+    p->maxTiles = N / TILE_MIN + p->maxSets + 16;
     QH_ALLOC(p->tbest, 4 * p->maxTiles);
     QH_ALLOC(p->text, p->maxTiles);
     QH_ALLOC(p->inst, p->maxSets);
     QH_ALLOC(p->bigInst, p->maxSets + 1);
     QH_ALLOC(p->smallInst, p->maxSets + 1);
     QH_ALLOC(p->bigTilePrefix, p->maxSets + 2);
-    // every big segment holds more than TILE points
-    p->maxBig = (int)(N / TILE + 16);
+    // every big segment holds more than a tile of points (the smallest tile of the variants)
+    p->maxBig = (int)(N / TILE_MIN + 16);
     long long bigSets = N / FIN_MAX + 1;
     if (bigSets > p->maxSets) bigSets = p->maxSets;
     long long nodes = 4 * bigSets + 16ll * 2 * p->maxBig + 4096;
@@ -184,10 +185,11 @@ qh_status run(qh_plan pl, const float *points, const long long *offsets, long lo
     if (e != cudaSuccess) return cuda_status(e);
     const bool tm = pl->timing != 0;
     if (tm) cudaEventRecord(pl->ev[0], s);
-    int per = rounds_max_ctas_per_sm(prec);
+    const RoundsVariant &V = rounds_variant(pl->variant);
+    int per = V.max_ctas_per_sm(prec);
     if (pl->ctasPerSm > 0 && pl->ctasPerSm < per) per = pl->ctasPerSm;
     if (per < 1) return QH_ERR_CUDA;
-    e = launch_rounds(p, prec, pl->numSMs * per, s);
+    e = V.launch(p, prec, pl->numSMs * per, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (tm) cudaEventRecord(pl->ev[1], s);
     e = launch_finish(p, prec, pl->numSMs, s);
@@ -274,11 +276,97 @@ qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags) {
 }
 
 qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int32_t grid_ctas_per_sm) {
-    if (!plan || cutover < TILE || cutover > FIN_MAX || grid_ctas_per_sm < 0) return QH_ERR_INVALID_ARG;
+    if (!plan || grid_ctas_per_sm < 0) return QH_ERR_INVALID_ARG;
+    if (cutover < rounds_variant(plan->variant).tile || cutover > FIN_MAX) return QH_ERR_INVALID_ARG;
     plan->cut = cutover;
     plan->timing = timing ? 1 : 0;
     plan->ctasPerSm = grid_ctas_per_sm;
     return QH_OK;
+}
+
+qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block) {
+    if (!plan) return QH_ERR_INVALID_ARG;
+    for (int v = 0; v < NUM_ROUNDS_VARIANTS; v++)
+        if (rounds_variant(v).threads == threads_per_block) {
+            plan->variant = v;
+            if (plan->cut < rounds_variant(v).tile) plan->cut = rounds_variant(v).tile;
+            plan->ctasPerSm = 0;
+            return QH_OK;
+        }
+    return QH_ERR_INVALID_ARG;
+}
+
+qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *items_per_thread, int32_t *cutover,
+                             int32_t *grid_ctas_per_sm) {
+    if (!plan) return QH_ERR_INVALID_ARG;
+    const RoundsVariant &V = rounds_variant(plan->variant);
+    if (threads_per_block) *threads_per_block = V.threads;
+    if (items_per_thread) *items_per_thread = V.tile / V.threads;
+    if (cutover) *cutover = plan->cut;
+    if (grid_ctas_per_sm) {
+        const int mx = V.max_ctas_per_sm((plan->flags & QH_PREC_F64) ? 1 : 0);
+        *grid_ctas_per_sm = (plan->ctasPerSm > 0 && plan->ctasPerSm < mx) ? plan->ctasPerSm : mx;
+    }
+    return QH_OK;
+}
+
+// Time every candidate setting (grid-kernel variant, grid CTAs per SM, small-segment cutover) on the
+// caller's input and keep the fastest in the plan.  The outputs are written by every trial; after the
+// call they hold the result of the last one, which is the same hull (every setting is exact).
+qh_status qh_plan_autotune(qh_plan plan, const float *points, const int64_t *offsets, int32_t num_sets, int64_t n,
+                           int32_t *out_idx, int32_t *out_counts, int32_t reps, qh_stream_t stream) {
+    if (!plan || reps < 1 || reps > 64) return QH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto call = [&]() -> qh_status {
+        return offsets ? qh_hull2d_batched(plan, points, offsets, num_sets, out_idx, out_counts, stream)
+                       : qh_hull2d_p(plan, points, n, out_idx, out_counts, stream);
+    };
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return QH_ERR_CUDA;
+    }
+    const int saveTiming = plan->timing;
+    plan->timing = 0;
+    float best = -1.f;
+    int bestV = plan->variant, bestCut = plan->cut, bestCtas = plan->ctasPerSm;
+    qh_status st = QH_OK;
+    const int prec = (plan->flags & QH_PREC_F64) ? 1 : 0;
+    for (int v = 0; v < NUM_ROUNDS_VARIANTS && st == QH_OK; v++) {
+        const RoundsVariant &V = rounds_variant(v);
+        const int mx = V.max_ctas_per_sm(prec);
+        for (int ctas = mx; ctas >= 1 && ctas >= mx / 2 && st == QH_OK; ctas--) {
+            for (int cut = V.tile; cut <= FIN_MAX && st == QH_OK; cut += 1024) {
+                plan->variant = v;
+                plan->ctasPerSm = ctas;
+                plan->cut = cut;
+                st = call();  // warm-up (first use of the variant, caches)
+                float tot = 0.f;
+                for (int r = 0; r < reps && st == QH_OK; r++) {
+                    cudaEventRecord(a, s);
+                    st = call();
+                    cudaEventRecord(b, s);
+                    if (cudaEventSynchronize(b) != cudaSuccess) st = QH_ERR_CUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, a, b);
+                    tot += ms;
+                }
+                if (st == QH_OK && (best < 0.f || tot < best)) {
+                    best = tot;
+                    bestV = v;
+                    bestCut = cut;
+                    bestCtas = ctas;
+                }
+            }
+        }
+    }
+    plan->variant = bestV;
+    plan->cut = bestCut;
+    plan->ctasPerSm = bestCtas;
+    plan->timing = saveTiming;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
 }
 
 qh_status qh_hull2d_p(qh_plan plan, const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
@@ -457,9 +545,6 @@ qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_
 }  // extern "C"
 
 #ifdef QH_PROFILE
-namespace qh {
-int prof_cta_copy(void *host, int n);
-}
 // Profiling builds only: per-CTA records of the initial split (8 x uint64 per CTA).
-extern "C" int qh_debug_prof_cta(void *host, int n) { return qh::prof_cta_copy(host, n); }
+extern "C" int qh_debug_prof_cta(void *host, int n) { return qh::v256::prof_cta_copy(host, n); }
 #endif

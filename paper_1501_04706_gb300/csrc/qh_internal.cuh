@@ -14,6 +14,8 @@ namespace qh {
 // ---------------------------------------------------------------------------
 // Tunables
 // ---------------------------------------------------------------------------
+// The grid-wide kernel is compiled once per variant (threads per CTA, CTAs per
+// SM); QH_NT / QH_MINB select the variant of a translation unit.
 #ifndef QH_NT
 #define QH_NT 256
 #endif
@@ -25,6 +27,7 @@ constexpr int MINB = QH_MINB;      // CTAs per SM the grid-wide kernel is built 
 constexpr int NWARP = NT / 32;
 constexpr int IPT = 16;            // points per thread per tile (warp-striped rows)
 constexpr int TILE = NT * IPT;     // points per tile
+constexpr int TILE_MIN = 128 * IPT;  // smallest tile of the compiled variants (sizes the plans)
 constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
 constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
 constexpr int MAX_LEVELS = 48;     // grid-wide rounds (deeper recursions report QH_ERR_CAPACITY)
@@ -308,8 +311,30 @@ __device__ __forceinline__ unsigned pkey_up(float f) { return fkey(f); }
 __device__ __forceinline__ unsigned pkey_up(double d) { return fkey(__double2float_ru(d)); }
 
 // Host launchers (defined in the .cu files).
+// Grid-wide kernel variants: 256 threads x 16 points per tile (2 CTAs per SM)
+// and 128 threads x 16 points per tile (4 CTAs per SM).
+namespace v256 {
 cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
 int rounds_max_ctas_per_sm(int prec);
+int prof_cta_copy(void *host, int n);
+}  // namespace v256
+namespace v128 {
+cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
+int rounds_max_ctas_per_sm(int prec);
+int prof_cta_copy(void *host, int n);
+}  // namespace v128
+struct RoundsVariant {
+    int threads, tile;
+    cudaError_t (*launch)(const Params &, int, int, cudaStream_t);
+    int (*max_ctas_per_sm)(int);
+};
+constexpr int NUM_ROUNDS_VARIANTS = 2;
+inline const RoundsVariant &rounds_variant(int v) {
+    static const RoundsVariant table[NUM_ROUNDS_VARIANTS] = {
+        {256, 256 * IPT, &v256::launch_rounds, &v256::rounds_max_ctas_per_sm},
+        {128, 128 * IPT, &v128::launch_rounds, &v128::rounds_max_ctas_per_sm}};
+    return table[v];
+}
 cudaError_t launch_finish(const Params &p, int prec, int grid, cudaStream_t s);
 int finish_smem_bytes();
 cudaError_t launch_emit(const Params &p, cudaStream_t s);

@@ -9,7 +9,8 @@
 // (the array is part of the library's device image: every GPU that loads the
 // library holds it, about 16 MB, until the process exits).
 //
-// The work itself is the library's regular kernel sequence (grid-wide rounds,
+// The work itself is the library's regular kernel sequence (grid-wide rounds in
+// the 256-thread variant,
 // block finisher, emit, copy) with the quadrilateral initial split and FP32
 // filtered predicates, so its results are those of qh_hull2d.
 #include <cuda_runtime.h>
@@ -85,7 +86,7 @@ qh_status na_setup(int dev, DeviceScratch &d) {
     if (e != cudaSuccess || ptr == nullptr) return QH_ERR_CUDA;
     e = cudaDeviceGetAttribute(&d.numSMs, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return QH_ERR_CUDA;
-    d.ctasPerSm = rounds_max_ctas_per_sm(0);
+    d.ctasPerSm = v256::rounds_max_ctas_per_sm(0);
     if (d.ctasPerSm < 1) return QH_ERR_CUDA;
     d.base = static_cast<unsigned char *>(ptr);
     d.ready = true;
@@ -158,7 +159,7 @@ extern "C" qh_status qh_hull2d_noalloc(const float *points, int64_t n, int32_t *
     // (counters, barrier, statistics, error bits); every other buffer is
     // initialised by the kernels before it is read
     cudaError_t e = cudaMemsetAsync(p.ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = launch_rounds(p, 0, d.numSMs * d.ctasPerSm, s);
+    if (e == cudaSuccess) e = v256::launch_rounds(p, 0, d.numSMs * d.ctasPerSm, s);
     if (e == cudaSuccess) e = launch_finish(p, 0, d.numSMs, s);
     if (e == cudaSuccess) e = launch_emit(p, s);
     if (e == cudaSuccess) e = launch_copy(p, d.numSMs * 4, s);

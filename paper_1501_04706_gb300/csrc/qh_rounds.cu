@@ -36,7 +36,12 @@
 // for the block finisher, so a tile of a round spans at most two segments.
 #include "qh_internal.cuh"
 
+#ifndef QH_VARIANT_NS
+#define QH_VARIANT_NS v256
+#endif
+
 namespace qh {
+namespace QH_VARIANT_NS {
 
 #ifdef QH_PROFILE
 __device__ unsigned long long *qh_ctl_prof;
@@ -1900,7 +1905,9 @@ cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s) {
                                        sizeof(RoundSmem<float>), s);
 }
 
-#ifdef QH_PROFILE
+#ifndef QH_PROFILE
+int prof_cta_copy(void *, int) { return -1; }
+#else
 int prof_cta_copy(void *host, int n) {
     return cudaMemcpyFromSymbol(host, qh_prof_cta, sizeof(unsigned long long) * 8 * (size_t)min(n, 1024)) ==
                    cudaSuccess
@@ -1921,4 +1928,5 @@ int rounds_max_ctas_per_sm(int prec) {
     return b;
 }
 
+}  // namespace QH_VARIANT_NS
 }  // namespace qh

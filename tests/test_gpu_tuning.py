@@ -1,0 +1,78 @@
+"""Block-size variants of the grid-wide kernel, the cutover range and the
+autotuner: every setting gives the oracle's hull and live counts."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("name", ["square", "disk", "circle", "degenerate"])
+@pytest.mark.parametrize("mode", ["quad", "chord"])
+def test_block_128_matches_oracle(qh, name, mode):
+    p = synth.make(name, 300_000, seed=5)
+    plan = qh.Plan(len(p), 1, mode=qh.MODE_QUAD if mode == "quad" else qh.MODE_CHORD)
+    plan.set_block(128)
+    t = plan.tuning()
+    assert t["threads_per_block"] == 128 and t["items_per_thread"] == 16 and t["cutover"] >= 2048
+    for cut in (2048, 3072, 4096):
+        plan.set_tuning(cut)
+        got = qh.hull2d(_dev(p), plan).cpu().numpy()
+        st = plan.stats()
+        want, live = oracle.quickhull(p, mode)
+        assert np.array_equal(got, want), cut
+        assert st["device_status"] == 0
+        assert st["live"] == live.tolist(), cut
+    plan.close()
+
+
+def test_cutover_range_follows_block_size(qh):
+    plan = qh.Plan(10_000, 1)
+    with pytest.raises(qh.QhError):
+        plan.set_tuning(2048)  # below the 4096-point tile of the 256-thread kernel
+    plan.set_block(128)
+    plan.set_tuning(2048)
+    assert plan.tuning()["cutover"] == 2048
+    plan.set_block(256)  # raises the cutover to the tile
+    assert plan.tuning()["cutover"] == 4096
+    with pytest.raises(qh.QhError):
+        plan.set_block(192)
+    plan.close()
+
+
+def test_autotune_single_set(qh):
+    p = synth.disk(500_000, seed=6)
+    plan = qh.Plan(len(p), 1)
+    d = _dev(p)
+    t = plan.autotune(d, reps=2)
+    assert t["threads_per_block"] in (128, 256)
+    assert t["threads_per_block"] * t["items_per_thread"] <= t["cutover"] <= 4096
+    assert t["grid_ctas_per_sm"] >= 1
+    assert np.array_equal(qh.hull2d(d, plan).cpu().numpy(), oracle.hull2d(p))
+    plan.close()
+
+
+def test_autotune_batched(qh):
+    import torch
+
+    p, off = synth.batched(200, seed=7, min_size=16, max_size=60_000)
+    plan = qh.Plan(len(p), 200)
+    d, doff = _dev(p), torch.from_numpy(off).cuda()
+    t = plan.autotune(d, doff, reps=1)
+    assert t["threads_per_block"] in (128, 256)
+    out, counts = qh.hull2d_batched(d, doff, plan)
+    out, counts = out.cpu().numpy(), counts.cpu().numpy()
+    want_out, want_counts = oracle.hull2d_batched(p, off)
+    assert np.array_equal(counts, want_counts)
+    for s in range(len(counts)):
+        a = int(off[s])
+        assert np.array_equal(out[a:a + counts[s]], want_out[a:a + counts[s]]), s
+    plan.close()
