@@ -55,6 +55,10 @@ __device__ unsigned long long qh_prof_cta[1024][8];
 constexpr int NS = 2;          // pipeline stages per CTA
 constexpr int DB = NT >= 256 ? 8 : 4;  // tile descriptors resolved per batch (one thread per tile)
 constexpr int CLS_NONE = 15;
+#ifndef QH_UNROLL
+#define QH_UNROLL 4
+#endif
+constexpr int UNROLL_ITEMS = QH_UNROLL;  // items of a thread handled per iteration of the per-tile loops
 constexpr int CQ = NT >= 256 ? 16 : 12;  // farthest-point candidates kept per slot before the fallback
 
 // Items of one segment inside a tile: physical range [q0, q0 + c) of the
@@ -896,21 +900,19 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
 // Record the slot c (CLS_NONE: discarded) of item j with the keys of its
 // distance bounds.
 __device__ __forceinline__ void note_item(int j, int c, unsigned klo, unsigned khi, unsigned &cp0, unsigned &cp1,
-                                          unsigned &cnt, unsigned (&mlo)[4], unsigned (&mhi)[4]) {
+                                          unsigned &cnt, unsigned (&mlo)[4], unsigned &mhi) {
     const unsigned v = (unsigned)c << (4 * (j & 7));
     cp0 |= j < 8 ? v : 0u;
     cp1 |= j < 8 ? 0u : v;
     cnt += c < 4 ? 1u << (8 * c) : 0u;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        mlo[q] = c == q ? max(mlo[q], klo) : mlo[q];
-        mhi[q] = c == q ? max(mhi[q], khi) : mhi[q];
-    }
+    for (int q = 0; q < 4; q++) mlo[q] = c == q ? max(mlo[q], klo) : mlo[q];
+    mhi = c < 4 ? max(mhi, khi) : mhi;
 }
 
 // The same for an item j known only at run time whose slot was CLS_NONE.
 __device__ __forceinline__ void renote_item(int j, int c, unsigned klo, unsigned khi, unsigned &cp0, unsigned &cp1,
-                                            unsigned &cnt, unsigned (&mlo)[4], unsigned (&mhi)[4]) {
+                                            unsigned &cnt, unsigned (&mlo)[4], unsigned &mhi) {
     const unsigned sh = 4u * (unsigned)(j & 7);
     const unsigned m = ~(15u << sh) | ((unsigned)c << sh);
     if (j < 8)
@@ -921,10 +923,8 @@ __device__ __forceinline__ void renote_item(int j, int c, unsigned klo, unsigned
         cnt += 1u << (8 * c);
 #pragma unroll
         for (int q = 0; q < 4; q++)
-            if (c == q) {
-                mlo[q] = max(mlo[q], klo);
-                mhi[q] = max(mhi[q], khi);
-            }
+            if (c == q) mlo[q] = max(mlo[q], klo);
+        mhi = max(mhi, khi);
     }
 }
 
@@ -1053,12 +1053,13 @@ __device__ __forceinline__ void offer_candidate(RoundSmem<P> &sm, int c, unsigne
     }
 }
 
-// Slots in which this thread holds an item whose upper-bound key reaches the
-// slot's threshold (bit q for slot q).
-__device__ __forceinline__ unsigned candidate_slots(const unsigned (&mhi)[4], const unsigned (&thr)[4]) {
+// Slots in which this thread may hold an item whose upper-bound key reaches the
+// slot's threshold (bit q for slot q): it holds items of the slot and the
+// largest upper-bound key over all its items reaches the threshold (a superset).
+__device__ __forceinline__ unsigned candidate_slots(unsigned mhi, unsigned cnt, const unsigned (&thr)[4]) {
     unsigned f = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; q++) f |= (unsigned)((mhi[q] != 0u) & (mhi[q] >= thr[q])) << q;
+    for (int q = 0; q < 4; q++) f |= (unsigned)((((cnt >> (8 * q)) & 0xffu) != 0u) & (mhi >= thr[q])) << q;
     return f;
 }
 
@@ -1237,7 +1238,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
         // taken in increasing index order, so strict comparisons keep the lowest
         // index among equal coordinates.
         unsigned hm = 0u;
-#pragma unroll 4
+#pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const float2 v = xs[i + dx];  // inside the stage for every j
@@ -1341,8 +1342,8 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         const float botx = R.poly[1].x, topx = R.poly[(iB + 1) & 3].x;
         const float2 *xs = sm.stage[s].xy;
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
-        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
-#pragma unroll 4
+        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi = 0u;
+#pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
@@ -1385,7 +1386,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         float2 *oxy = p.xy[0];
         int *oid = p.id[0];
         bool bad = false;
-#pragma unroll 4
+#pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
@@ -1401,7 +1402,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             }
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
-        if (const unsigned fl = candidate_slots(mhi, thr)) {
+        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
             for (int j = 0; j < IPT; j++) {
                 const int c = item_cls(j, cp0, cp1);
                 if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
@@ -1524,8 +1525,8 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         const int *is = sm.stage[s].id;
         // pass 1: strictly right of h->c (first child) or of c->e (second child)
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
-        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi[4] = {0u, 0u, 0u, 0u};
-#pragma unroll 4
+        unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi = 0u;
+#pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
@@ -1569,7 +1570,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         int *oid = p.id[dst];
         const long long lim = 2 * p.ncap;
         bool bad = false;
-#pragma unroll 4
+#pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
@@ -1589,7 +1590,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             }
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
-        if (const unsigned fl = candidate_slots(mhi, thr)) {
+        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
             for (int j = 0; j < IPT; j++) {
                 const int c = item_cls(j, cp0, cp1);
                 if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
