@@ -90,6 +90,14 @@ struct TileRec {
 };
 
 constexpr int STAGE_PAD = 16;  // room for the rounded-out ends of two parts
+// The set of the last resolved set tile (descriptor batches of the extreme-point
+// pass and the initial split): consecutive tiles mostly belong to one set.
+struct SetCache {
+    long long tile0, setOff, setN;
+    int tiles, inst, K, iB, valid, pad;
+    Cand poly[4];
+};
+
 struct StageBuf {
     float2 xy[TILE + STAGE_PAD];
     int id[TILE + STAGE_PAD];
@@ -122,6 +130,7 @@ template <typename P> struct RunAcc {
 template <typename P> struct RoundSmem {
     unsigned long long mbar[NS];
     RunAcc<P> run;
+    SetCache setc;
     TileRec desc[2][DB];  // descriptors of the CTA's tiles, double-buffered by batch
     // tile working set
     Edge<P> edge[4];   // per slot: the edge a point of the slot lies strictly right of
@@ -637,30 +646,41 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
 // (binary searches, segment records) of DB tiles overlap; thread 0 then only
 // copies a descriptor and starts its TMA copies.
 // --------------------------------------------------------------------------
-__device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool withPoly) {
-    const int nBig = __ldcg(&p.ctl->nBig);
-    const long long j = upper_bound_ll(p.bigTilePrefix, nBig + 1, t) - 1;
-    const int i = __ldcg(&p.bigInst[j]);
-    const Inst *I = &p.inst[i];
+__device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool withPoly, const SetCache &sc) {
     R.t = t;
-    R.inst = i;
     R.np = 1;
     R.valid = 1;
     R.srcBuf = 0;
-    R.lt = t - __ldcg(&p.bigTilePrefix[j]);
-    R.setOff = __ldcg(&I->off);
-    R.setN = __ldcg(&I->n);
-    R.tile0 = __ldcg(&I->tile0);
-    R.tiles = __ldcg(&I->tiles);
     R.K = 0;
     R.iB = 1;
-    if (withPoly) {
-        R.K = __ldcg(&I->K);
-        R.iB = __ldcg(&I->iB);
-        for (int k = 0; k < 4; k++) {
-            R.poly[k] = ldcg_cand(&I->poly[k]);
+    if (sc.valid && t >= sc.tile0 && t < sc.tile0 + sc.tiles) {  // the cached set: no lookups
+        R.inst = sc.inst;
+        R.setOff = sc.setOff;
+        R.setN = sc.setN;
+        R.tile0 = sc.tile0;
+        R.tiles = sc.tiles;
+        if (withPoly) {
+            R.K = sc.K;
+            R.iB = sc.iB;
+            for (int k = 0; k < 4; k++) R.poly[k] = sc.poly[k];
+        }
+    } else {
+        const int nBig = __ldcg(&p.ctl->nBig);
+        const long long j = upper_bound_ll(p.bigTilePrefix, nBig + 1, t) - 1;
+        const int i = __ldcg(&p.bigInst[j]);
+        const Inst *I = &p.inst[i];
+        R.inst = i;
+        R.setOff = __ldcg(&I->off);
+        R.setN = __ldcg(&I->n);
+        R.tile0 = __ldcg(&I->tile0);
+        R.tiles = __ldcg(&I->tiles);
+        if (withPoly) {
+            R.K = __ldcg(&I->K);
+            R.iB = __ldcg(&I->iB);
+            for (int k = 0; k < 4; k++) R.poly[k] = ldcg_cand(&I->poly[k]);
         }
     }
+    R.lt = t - R.tile0;
     const long long first = R.lt * TILE;
     const int c = (int)min((long long)TILE, R.setN - first);
     R.nItems = c;
@@ -764,9 +784,25 @@ template <typename P> __device__ void resolve_batch(const Params &p, const TileS
         if (q.kind == 2)
             resolve_round_tile(p, desc_of(sm, k0 + j), t, q.S, q.L, q.cur, q.src);
         else
-            resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1);
+            resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1, sm.setc);
     }
     __syncthreads();
+    if (q.kind != 2 && threadIdx.x == 0) {  // cache the set of the batch's last tile
+        const long long last = min(q.cnt, k0 + DB) - 1;
+        if (last >= k0) {
+            const TileRec &R = desc_of(sm, last);
+            SetCache &c = sm.setc;
+            c.tile0 = R.tile0;
+            c.setOff = R.setOff;
+            c.setN = R.setN;
+            c.tiles = R.tiles;
+            c.inst = R.inst;
+            c.K = R.K;
+            c.iB = R.iB;
+            for (int k = 0; k < 4; k++) c.poly[k] = R.poly[k];
+            c.valid = 1;
+        }
+    }
 }
 
 // Start the pipeline: first batch of descriptors, then the first NS tiles.
@@ -778,7 +814,10 @@ template <typename P>
 __device__ void pipe_start(const Params &p, const TileSeq &q, unsigned long long &gI) {
     RoundSmem<P> &sm = round_smem<P>();
     if (q.cnt <= 0) return;
-    if (threadIdx.x == 0) fence_proxy_async();
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        sm.setc.valid = 0;  // sets change between phases (the polygon appears after the extreme points)
+    }
     resolve_batch<P>(p, q, 0);
     for (long long j = 0; j < min(q.cnt, (long long)NS); j++) {
         if (threadIdx.x == 0) issue_desc<P>(p, (int)(gI % NS), desc_of(sm, j), q.kind != 2);
@@ -926,6 +965,25 @@ __device__ __forceinline__ void renote_item(int j, int c, unsigned klo, unsigned
             if (c == q) mlo[q] = max(mlo[q], klo);
         mhi = max(mhi, khi);
     }
+}
+
+// Bit k of the result: nibble k of w equals q (an exact zero-nibble test:
+// adding 7 to the low three bits of a nibble never carries out of it).
+__device__ __forceinline__ unsigned nibbles_equal(unsigned w, unsigned q) {
+    const unsigned x = w ^ (0x11111111u * q);
+    unsigned t = (~(((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u) >> 3;  // bit 4k
+    t = (t | (t >> 3)) & 0x03030303u;
+    t = (t | (t >> 6)) & 0x000f000fu;
+    return (t | (t >> 12)) & 0xffu;
+}
+
+// Items (bit j) of this thread whose slot is in the set fl.
+__device__ __forceinline__ unsigned items_in_slots(unsigned fl, unsigned cp0, unsigned cp1) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if ((fl >> q) & 1u) m |= nibbles_equal(cp0, q) | (nibbles_equal(cp1, q) << 8);
+    return m;
 }
 
 __device__ __forceinline__ int item_cls(int j, unsigned cp0, unsigned cp1) {
@@ -1403,9 +1461,9 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
         if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
-            for (int j = 0; j < IPT; j++) {
+            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
+                const int j = __ffs(m) - 1;
                 const int c = item_cls(j, cp0, cp1);
-                if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
                 const int i = j * NT + threadIdx.x;
                 const float2 v = xs[i + dx];
                 offer_candidate(sm, c, sel4(c, thr), v.x, v.y, idBase + i);
@@ -1591,9 +1649,9 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
         if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
-            for (int j = 0; j < IPT; j++) {
+            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
+                const int j = __ffs(m) - 1;
                 const int c = item_cls(j, cp0, cp1);
-                if (!((fl >> c) & 1u)) continue;  // CLS_NONE shifts past the four slot bits
                 const int i = j * NT + threadIdx.x;
                 const bool pb = (c == 2) | (c == 3);
                 const float2 v = xs[i + (pb ? dx1 : dx0)];
