@@ -50,6 +50,12 @@ __device__ __forceinline__ unsigned long long *round_ctl_prof() { return qh_ctl_
 // first tile, tiles, exact orientations, exact comparisons, pass-1 and
 // pass-2 cycles.
 __device__ unsigned long long qh_prof_cta[1024][8];
+// Phase timeline (profiling builds only): rows 512 + 2 ph (latest over the
+// CTAs) and 513 + 2 ph (earliest) of qh_prof_cta hold, per event, the ns since
+// the kernel's start stamp plus 2^40.
+#define QH_TL(ph, e) tl_event(p, ph, e)
+#else
+#define QH_TL(ph, e)
 #endif
 
 constexpr int NS = 2;          // pipeline stages per CTA
@@ -187,12 +193,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
         : "memory");
     return ok != 0u;
 }
-// 1-D bulk copy global -> shared, completing on mbarrier b (16-byte aligned, size % 16 == 0).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(b))
-                 : "memory");
+// L2 policy of the tile copies: every tile is read once per pass, so its lines
+// go first and the round outputs, tables and code stay in L2.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// 1-D bulk copy global -> shared, completing on mbarrier b (16-byte aligned, size % 16 == 0),
+// with L2 cache policy pol.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b,
+                                         unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b)), "l"(pol)
+        : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
@@ -399,6 +415,14 @@ template <typename P> __device__ __forceinline__ ICand<P> shfl_icand(const ICand
 
 // Chunk of tiles of CTA b: [floor(b T / G), floor((b + 1) T / G)).
 __device__ __forceinline__ long long chunk_start(long long b, long long T, long long G) { return b * T / G; }
+// The same in 32-bit arithmetic (a 64-bit division is a long dependent chain)
+// when b * T fits: narrow = G * T < 2^32.
+__device__ __forceinline__ long long chunk_start_n(long long b, long long T, long long G, bool narrow) {
+    return narrow ? (long long)((unsigned)b * (unsigned)T / (unsigned)G) : b * T / G;
+}
+// Records of a parent a thread keeps in registers while merging (one per CTA
+// of the largest grid of the variant, NT per pass).
+constexpr int MREC = (152 * MINB + NT - 1) / NT;
 // The chunk holding tile t: the largest b with chunk_start(b) <= t.
 __device__ __forceinline__ long long chunk_of(long long t, long long T, long long G) {
     return min(((t + 1) * G + T - 1) / T - 1, G - 1);
@@ -407,9 +431,10 @@ __device__ __forceinline__ long long chunk_of(long long t, long long T, long lon
 // Farthest point of every child of a parent spanning tiles [ta, tb] -> sm.fin.
 // The parent's runs start at ta (record slots slotBase0..) and at every chunk
 // start inside (ta, tb] (slots 0..), each holding the exact best of its tiles.
-// All records are read at once; only those whose upper bound reaches the
+// All records are read at once (every load of a thread in flight together) and
+// their bound keys kept in registers; only those whose upper bound reaches the
 // child's largest lower bound can be its farthest point, and only these are
-// compared (exactly) by one thread per child.
+// read again and compared (exactly) by one thread per child.
 template <typename P>
 __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long tb, int slotBase0, int nslot,
                                         int edgeOff, long long T, int &exact_c) {
@@ -418,12 +443,21 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
     const long long G = gridDim.x;
     const long long c0 = chunk_of(ta, T, G), c1 = chunk_of(tb, T, G);
     const long long nrec = 1 + (c1 - c0);  // record 0 at ta, then the chunks c0 + 1 .. c1
+#ifdef QH_PROFILE
+    unsigned long long mt[6];
+    mt[0] = global_ns();
+#define QH_MT(k) mt[k] = global_ns()
+#else
+#define QH_MT(k)
+#endif
     if (threadIdx.x < 4) {
         sm.mthr[threadIdx.x] = 0u;
         sm.nq[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
+    QH_MT(1);
+    const bool narrow = (unsigned long long)G * (unsigned long long)(T + 1) < (1ull << 32);
     // record r: its tile (-1: none) and record slot base
     auto rec_tile = [&](long long r, int &base) -> long long {
         base = 0;
@@ -431,11 +465,41 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
             base = slotBase0;
             return ta;
         }
-        const long long st = chunk_start(c0 + r, T, G);
-        return (st > ta && st < chunk_start(c0 + r + 1, T, G)) ? st : -1;  // a non-empty chunk starting inside
+        const long long st = chunk_start_n(c0 + r, T, G, narrow);
+        return (st > ta && st < chunk_start_n(c0 + r + 1, T, G, narrow)) ? st : -1;  // a non-empty chunk inside
     };
+    auto offer = [&](int q, const ICand<P> &ic) {
+        const int j = atomicAdd(&sm.nq[q], 1);
+        if (j < CQ)
+            sm.candq[q][j] = ic;
+        else
+            sm.candOver = 1;
+    };
+    // pass 1: records threadIdx.x + k NT (k < MREC) with their keys kept; any
+    // further records (larger grids) are read again in pass 2
     unsigned mlo[4] = {0u, 0u, 0u, 0u};
-    for (long long r = threadIdx.x; r < nrec; r += NT) {
+    unsigned khi[MREC][4];
+    long long rtile[MREC];
+    int rbase[MREC];
+#pragma unroll
+    for (int k = 0; k < MREC; k++) {
+        const long long r = threadIdx.x + (long long)k * NT;
+        rtile[k] = r < nrec ? rec_tile(r, rbase[k]) : -1;
+        Cand c[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            c[q] = (rtile[k] >= 0 && q < nslot) ? ldcg_cand(&p.tbest[4 * rtile[k] + rbase[k] + q]) : no_cand();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            khi[k][q] = 0u;
+            if (c[q].idx >= 0) {
+                const ICand<P> ic = icand_of(sm, edgeOff + q, c[q]);
+                mlo[q] = max(mlo[q], max(pkey(ic.lo), 1u));
+                khi[k][q] = max(pkey_up(ic.hi), 1u);
+            }
+        }
+    }
+    for (long long r = threadIdx.x + (long long)MREC * NT; r < nrec; r += NT) {
         int base;
         const long long tile = rec_tile(r, base);
         if (tile < 0) continue;
@@ -450,22 +514,27 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         if (lane == 0 && v) atomicMax(&sm.mthr[q], v);
     }
     __syncthreads();
-    for (long long r = threadIdx.x; r < nrec; r += NT) {
+    QH_MT(2);
+    // pass 2: the candidates among the kept records are read again (rare)
+#pragma unroll
+    for (int k = 0; k < MREC; k++) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (khi[k][q] != 0u && khi[k][q] >= sm.mthr[q])
+                offer(q, icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * rtile[k] + rbase[k] + q])));
+        }
+    }
+    for (long long r = threadIdx.x + (long long)MREC * NT; r < nrec; r += NT) {
         int base;
         const long long tile = rec_tile(r, base);
         if (tile < 0) continue;
         for (int q = 0; q < nslot; q++) {
             const ICand<P> ic = icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q]));
-            if (ic.c.idx >= 0 && pkey_up(ic.hi) >= sm.mthr[q]) {
-                const int j = atomicAdd(&sm.nq[q], 1);
-                if (j < CQ)
-                    sm.candq[q][j] = ic;
-                else
-                    sm.candOver = 1;
-            }
+            if (ic.c.idx >= 0 && pkey_up(ic.hi) >= sm.mthr[q]) offer(q, ic);
         }
     }
     __syncthreads();
+    QH_MT(3);
     if (!sm.candOver) {
         if (threadIdx.x < nslot) {
             const int q = threadIdx.x, n = sm.nq[q];
@@ -494,9 +563,16 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         }
     }
     __syncthreads();
+    QH_MT(4);
     if (threadIdx.x < 4) sm.nq[threadIdx.x] = 0;
     if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
+#ifdef QH_PROFILE
+    QH_MT(5);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; k++) atomicMax(&p.ctl->prof[33 + k], mt[k + 1] - mt[k]);
+#endif
+#undef QH_MT
 }
 
 // Publish the CTA's run (record + tile count on the parent's counter); the
@@ -519,6 +595,9 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
         sm.fflag[0] = old + (unsigned)ra.tiles == (unsigned)ra.total;
     }
     __syncthreads();
+#ifdef QH_PROFILE
+    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[42], global_ns() - tf0);
+#endif
     if (sm.fflag[0]) {
         __threadfence();
 #ifdef QH_PROFILE
@@ -527,6 +606,9 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
         merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
 #ifdef QH_PROFILE
         if (threadIdx.x == 0) atomicMax(&p.ctl->prof[30], global_ns() - tm0);
+        const unsigned long long tm1 = global_ns();
+        merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);  // again, warm
+        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[32], global_ns() - tm1);
 #endif
         if (threadIdx.x < nslot) {
             Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
@@ -749,17 +831,18 @@ __device__ void issue_desc(const Params &p, int s, const TileRec &R, bool set) {
     RoundSmem<P> &sm = round_smem<P>();
     mbar_expect_tx(&sm.mbar[s], R.bytes);
     if (R.bytes == 0u) return;
+    const unsigned long long pol = l2_evict_first();
     if (set) {
         const PartGeo &g = R.g[0];
-        bulk_g2s(&sm.stage[s].xy[g.sx], p.pts + g.a0, (unsigned)g.na * 8u, &sm.mbar[s]);
+        bulk_g2s(&sm.stage[s].xy[g.sx], p.pts + g.a0, (unsigned)g.na * 8u, &sm.mbar[s], pol);
         return;
     }
     const float2 *gxy = p.xy[R.srcBuf];
     const int *gid = p.id[R.srcBuf];
     for (int part = 0; part < R.np; part++) {
         const PartGeo &g = R.g[part];
-        if (g.na > 0) bulk_g2s(&sm.stage[s].xy[g.sx], gxy + g.a0, (unsigned)g.na * 8u, &sm.mbar[s]);
-        if (g.nb > 0) bulk_g2s(&sm.stage[s].id[g.si], gid + g.b0, (unsigned)g.nb * 4u, &sm.mbar[s]);
+        if (g.na > 0) bulk_g2s(&sm.stage[s].xy[g.sx], gxy + g.a0, (unsigned)g.na * 8u, &sm.mbar[s], pol);
+        if (g.nb > 0) bulk_g2s(&sm.stage[s].id[g.si], gid + g.b0, (unsigned)g.nb * 4u, &sm.mbar[s], pol);
     }
 }
 
@@ -837,6 +920,19 @@ __device__ void pipe_refill(const Params &p, const TileSeq &q, long long k, int 
     gI++;
 }
 
+#ifdef QH_PROFILE
+__device__ __forceinline__ void tl_event(const Params &p, int ph, int e) {
+    if (threadIdx.x == 0 && ph < 32) {
+        const unsigned long long v = global_ns() - __ldcg(&p.ctl->tphase[0]) + (1ull << 40);
+        atomicMax(&qh_prof_cta[512 + 2 * ph][e], v);
+        atomicMin(&qh_prof_cta[513 + 2 * ph][e], v);
+    }
+}
+__device__ void tl_reset() {
+    for (int k = threadIdx.x; k < 64 * 8; k += NT) qh_prof_cta[512 + k / 8][k % 8] = (k / 8) & 1 ? ~0ull : 0ull;
+}
+#endif
+
 // Wait for every copy still in flight (used on the error path before leaving).
 template <typename P>
 __device__ void pipe_drain(const Params &p, unsigned long long gI, unsigned long long gC) {
@@ -859,7 +955,13 @@ template <typename P>
 __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long segFirst, int segTiles) {
     RoundSmem<P> &sm = round_smem<P>();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    QH_PROF_DECL;
+#ifdef QH_PROFILE
+    unsigned long long et[6];
+    et[0] = global_ns();
+#define QH_ET(k) et[k] = global_ns()
+#else
+#define QH_ET(k)
+#endif
     e = warp_ext_reduce(e);
     __syncthreads();
     if (lane == 0) sm.wext[w] = e;
@@ -874,8 +976,13 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         __threadfence();
     }
     __syncthreads();
-    if (!sm.kflag) return;
-    QH_PROF(0);
+    QH_ET(1);
+    if (!sm.kflag) {
+#ifdef QH_PROFILE
+        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[43], et[1] - et[0]);
+#endif
+        return;
+    }
     const Inst *I = &p.inst[i];
     const long long tile0 = __ldcg(&I->tile0);
     const long long tiles = __ldcg(&I->tiles);
@@ -886,13 +993,13 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         const long long c = b * T / G;  // chunk starts inside the set hold partials too
         if (c > tile0 && c < tile0 + tiles) ext_merge(r, ld_ext(&p.text[c]));
     }
-    QH_PROF(1);
+    QH_ET(2);
     r = warp_ext_reduce(r);
-    QH_PROF(2);
+    QH_ET(3);
     __syncthreads();
     if (lane == 0) sm.wext[w] = r;
     __syncthreads();
-    QH_PROF(3);
+    QH_ET(4);
     if (threadIdx.x == 0) {
         Ext a = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(a, sm.wext[k]);
@@ -918,10 +1025,15 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         W.iB = iB;
         for (int k = 0; k < 4; k++) W.poly[k] = (k < K || (kind == I_DEGEN && k == 0)) ? poly[k] : no_cand();
         __threadfence();
-        QH_PROF(6);
     }
     __syncthreads();
-    QH_PROF(7);
+    QH_TL(0, 4);
+#ifdef QH_PROFILE
+    QH_ET(5);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; k++) atomicMax(&p.ctl->prof[43 + k], et[k + 1] - et[k]);
+#endif
+#undef QH_ET
 }
 
 // --------------------------------------------------------------------------
@@ -1237,6 +1349,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
     q.kind = 0;
     q.S = q.cur = q.src = 0;
     q.L = 0;
+    QH_TL(0, 0);
     tile_extremes_reset(sm);
     pipe_start<P>(p, q, gI);
     Ext acc = ext_empty();
@@ -1252,6 +1365,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
             return false;
         }
         QH_PROF(0);
+        if (k == 0) QH_TL(0, 1);
         const TileRec &R = desc_of(sm, k);
         const int inst = R.inst;
         if (inst != accInst) {
@@ -1327,7 +1441,9 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
 #ifdef QH_PROFILE
     const unsigned long long tLoop = global_ns();
 #endif
+    QH_TL(0, 2);
     if (accInst >= 0) ext_flush<P>(p, acc, accInst, segFirst, segTiles);
+    QH_TL(0, 3);
     QH_PROF(6);
     QH_PROF_FLUSH_AT(p.ctl, 8);
 #ifdef QH_PROFILE
@@ -1357,6 +1473,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
     q.kind = 1;
     q.S = q.cur = q.src = 0;
     q.L = 0;
+    QH_TL(1, 0);
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
     const unsigned lt = lanemask_lt();
@@ -1376,6 +1493,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             return false;
         }
         QH_PROF(0);
+        if (kt == 0) QH_TL(1, 1);
         tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int K = R.K, nItems = R.nItems;
@@ -1491,7 +1609,9 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         QH_PROF(1);
     }
     __syncthreads();
+    QH_TL(1, 2);
     if (sm.run.node >= 0) flush_run<P>(p, 1, T, exact_c);
+    QH_TL(1, 3);
     QH_PROF_FLUSH(p.ctl);
 #ifdef QH_PROFILE
     if (threadIdx.x == 0) {  // loop time in ns and in SM cycles (their ratio: the clock)
@@ -1543,6 +1663,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
     q.cur = cur;
     q.src = src;
     q.L = L;
+    QH_TL(r + 1, 0);
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
     const unsigned lt = lanemask_lt();
@@ -1555,6 +1676,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             pipe_drain<P>(p, gI, gC);
             return false;
         }
+        if (kt == 0) QH_TL(r + 1, 1);
         tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int valid = R.valid, np = R.np, nItems = R.nItems;
@@ -1684,7 +1806,9 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         pipe_refill<P>(p, q, kt, s, gI);
     }
     __syncthreads();
+    QH_TL(r + 1, 2);
     if (sm.run.node >= 0) flush_run<P>(p, 2, T, exact_c);
+    QH_TL(r + 1, 3);
     return true;
 }
 
@@ -1868,7 +1992,12 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     }
     __syncthreads();
     stamp(p.ctl, 0);
-    if (blockIdx.x == 0) prep<P>(p);
+    if (blockIdx.x == 0) {
+        prep<P>(p);
+#ifdef QH_PROFILE
+        tl_reset();
+#endif
+    }
     if (!grid_sync(p.ctl, phase)) goto out;
     stamp(p.ctl, 1);
 
@@ -1888,10 +2017,12 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     if (last_cta(p.ctl, donePhase, &sm.kflag)) {
 #ifdef QH_PROFILE
         const unsigned long long tb0 = global_ns();
+        QH_TL(1, 5);
 #endif
         build_level0<P>(p);
 #ifdef QH_PROFILE
         if (threadIdx.x == 0) p.ctl->prof[27] = global_ns() - tb0;
+        QH_TL(1, 4);
 #endif
     }
     if (!grid_sync(p.ctl, phase)) goto out;
@@ -1919,10 +2050,12 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         if (last_cta(p.ctl, donePhase, &sm.kflag)) {
 #ifdef QH_PROFILE
             const unsigned long long tb0 = global_ns();
+            QH_TL(r + 1, 5);
 #endif
             build_level<P>(p, r);
 #ifdef QH_PROFILE
             if (threadIdx.x == 0 && r <= 1) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
+            QH_TL(r + 1, 4);
 #endif
         }
         if (!grid_sync(p.ctl, phase)) goto out;
