@@ -88,7 +88,7 @@ struct Ext {
 struct Ctl {
     unsigned err;
     unsigned bar;        // grid barrier arrivals (monotonic within a launch)
-    unsigned done;       // CTAs finished with a phase (monotonic within a launch)
+    unsigned gen;        // barriers released by their leader (monotonic within a launch)
     int nBig, nSmallInst;
     int pad0;
     long long bigTiles;  // tiles over all big sets
@@ -252,6 +252,56 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase) {
         __threadfence();
         if (ld_volatile(&ctl->err) != 0u) ok = 0;
         s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Grid-wide barrier with a serial step: the last CTA to arrive (the leader)
+// returns 1 in all its threads, runs the step and calls grid_release; the
+// other CTAs wait for that release and return 0.  -1: an error was reported
+// or the wait timed out (the error bit is set).  One atomic round trip
+// instead of a separate "last CTA" count followed by a barrier.
+__device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase) {
+    __shared__ int s_role;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        phase++;
+        __threadfence();
+        const unsigned d = atomicAdd(&ctl->bar, 1u);
+        int role = 0;
+        if (d == phase * gridDim.x - 1u) {
+            role = 1;
+        } else {
+            unsigned it = 0;
+            while (ld_acquire(&ctl->gen) < phase) {
+                if (ld_volatile(&ctl->err) != 0u) {
+                    role = -1;
+                    break;
+                }
+                if (++it > SPIN_LIMIT) {
+                    set_err(ctl, E_TIMEOUT);
+                    role = -1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (ld_volatile(&ctl->err) != 0u) role = -1;
+        s_role = role;
+    }
+    __syncthreads();
+    return s_role;
+}
+// The leader's release (after its serial step); false when an error was reported.
+__device__ __forceinline__ bool grid_release(Ctl *ctl, unsigned phase) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(&ctl->gen, phase);
+        s_ok = ld_volatile(&ctl->err) == 0u;
     }
     __syncthreads();
     return s_ok != 0;

@@ -330,20 +330,6 @@ __device__ __forceinline__ Ext ld_ext(const Ext *p) {
 
 __device__ __forceinline__ bool same_xy(const Cand &a, const Cand &b) { return a.x == b.x && a.y == b.y; }
 
-// Returns true in every thread of the CTA that finished this phase last.
-__device__ __forceinline__ bool last_cta(Ctl *ctl, unsigned &donePhase, int *flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        donePhase++;
-        unsigned d = atomicAdd(&ctl->done, 1u);
-        *flag = (d == donePhase * gridDim.x - 1u);
-        __threadfence();
-    }
-    __syncthreads();
-    return *flag != 0;
-}
-
 // --------------------------------------------------------------------------
 // farthest-point candidates
 // --------------------------------------------------------------------------
@@ -1980,7 +1966,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
 #ifdef QH_PROFILE
     if (blockIdx.x == 0 && threadIdx.x == 0) qh_ctl_prof = p.ctl->prof;
 #endif
-    unsigned phase = 0, donePhase = 0;
+    unsigned phase = 0;
     int exact_o = 0, exact_c = 0;
     long long surv = 0;
     unsigned long long gI = 0, gC = 0;
@@ -2014,18 +2000,22 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
     }
     surv = 0;
-    if (last_cta(p.ctl, donePhase, &sm.kflag)) {
+    {
+        const int role = grid_arrive(p.ctl, phase);
+        if (role < 0) goto out;
+        if (role == 1) {  // the last CTA builds the first level
 #ifdef QH_PROFILE
-        const unsigned long long tb0 = global_ns();
-        QH_TL(1, 5);
+            const unsigned long long tb0 = global_ns();
+            QH_TL(1, 5);
 #endif
-        build_level0<P>(p);
+            build_level0<P>(p);
 #ifdef QH_PROFILE
-        if (threadIdx.x == 0) p.ctl->prof[27] = global_ns() - tb0;
-        QH_TL(1, 4);
+            if (threadIdx.x == 0) p.ctl->prof[27] = global_ns() - tb0;
+            QH_TL(1, 4);
 #endif
+            if (!grid_release(p.ctl, phase)) goto out;
+        }
     }
-    if (!grid_sync(p.ctl, phase)) goto out;
     stamp(p.ctl, 3);
 
     for (int r = 1;; r++) {
@@ -2047,7 +2037,9 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->gridRead += L;
         surv = 0;
-        if (last_cta(p.ctl, donePhase, &sm.kflag)) {
+        const int role = grid_arrive(p.ctl, phase);
+        if (role < 0) goto out;
+        if (role == 1) {  // the last CTA builds the next level
 #ifdef QH_PROFILE
             const unsigned long long tb0 = global_ns();
             QH_TL(r + 1, 5);
@@ -2057,8 +2049,8 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
             if (threadIdx.x == 0 && r <= 1) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
             QH_TL(r + 1, 4);
 #endif
+            if (!grid_release(p.ctl, phase)) goto out;
         }
-        if (!grid_sync(p.ctl, phase)) goto out;
         stamp(p.ctl, 3 + r);
     }
 out:
