@@ -24,9 +24,13 @@ struct OrdE {
     unsigned short head, live, c, pad;  // head point, live segment id (or NONE16), its farthest point
 };
 
+static_assert(FM % FIN_NT == 0, "the live list is split into FM / FIN_NT entries per thread");
+constexpr int FIN_PER = FM / FIN_NT;
+
 struct FinSmem {
     float2 pxy[FM + 2];
     unsigned short seg[FM];  // per point: live segment / child code, NONE16 = discarded
+    unsigned short lst[FM];  // the points still live (any order); nLive of them
     OrdE ordA[FM + 8], ordB[FM + 8];
     unsigned short lpos[FM];  // live segment -> position in the ord list
     unsigned cnt2[FM];        // per live segment: packed child counts (low: first child, high: second)
@@ -35,7 +39,7 @@ struct FinSmem {
     unsigned short newId[2 * FM];
     int scan[FIN_NT / 32 + 1];
     long long scan64[FIN_NT / 32 + 1];
-    int ticket, cLocal, nOrd, S, K, degenerate, nonfinite;
+    int ticket, cLocal, nOrd, S, K, degenerate, nonfinite, nLive;
     long long liveCount;
     unsigned short poly[4];
     Ext wext[FIN_NT / 32];
@@ -108,11 +112,13 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
     __syncthreads();
     // pass 1: classify.  The per-child counters are updated once per group of
     // lanes that share a child (same-address shared atomics would serialise).
-    for (int k0 = 0; k0 < m; k0 += FIN_NT) {
-        const int k = k0 + threadIdx.x;
+    const int nL = s.nLive;
+    for (int i0 = 0; i0 < nL; i0 += FIN_NT) {
+        const int i = i0 + threadIdx.x;
         int child = -1;
         unsigned key = 0u;
-        if (k < m) {
+        if (i < nL) {
+            const int k = s.lst[i];
             const unsigned short j = s.seg[k];
             if (j != NONE16) {
                 const float2 q = s.pxy[k];
@@ -170,7 +176,8 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
     }
     __syncthreads();
     // pass 2: exact farthest point among the candidates of each child
-    for (int k = threadIdx.x; k < m; k += FIN_NT) {
+    for (int i = threadIdx.x; i < nL; i += FIN_NT) {
+        const int k = s.lst[i];
         const unsigned short c = s.seg[k];
         if (c == NONE16) continue;
         int u, v;
@@ -274,10 +281,31 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
         if (threadIdx.x == 0) s.nOrd = tot;
     }
     __syncthreads();
-    // relabel points with their new live segment
-    for (int k = threadIdx.x; k < m; k += FIN_NT) {
-        const unsigned short c = s.seg[k];
-        if (c != NONE16) s.seg[k] = s.newId[c];
+    // relabel the points with their new live segment and keep the live ones
+    // in the list (a contiguous range of at most FIN_PER entries per thread,
+    // read before the scan's barriers and rewritten after them)
+    {
+        const int b = min(nL, (int)threadIdx.x * FIN_PER), e = min(nL, b + FIN_PER);
+        unsigned short keep[FIN_PER];
+        unsigned km = 0u;
+#pragma unroll
+        for (int j = 0; j < FIN_PER; j++) {
+            keep[j] = 0;
+            if (b + j < e) {
+                const unsigned short k = s.lst[b + j];
+                const unsigned short c = s.seg[k];
+                const unsigned short nc = c != NONE16 ? s.newId[c] : NONE16;
+                s.seg[k] = nc;
+                keep[j] = k;
+                km |= (unsigned)(nc != NONE16) << j;
+            }
+        }
+        int tot;
+        int x = block_excl_scan<int, FIN_NT>(__popc(km), s.scan, tot);
+#pragma unroll
+        for (int j = 0; j < FIN_PER; j++)
+            if ((km >> j) & 1u) s.lst[x++] = keep[j];
+        if (threadIdx.x == 0) s.nLive = tot;
     }
     if (threadIdx.x == 0)
         atomicAdd((unsigned long long *)&p.ctl->live[min(gen, MAX_GEN - 1)], (unsigned long long)s.liveCount);
@@ -327,9 +355,11 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     Ext ex;
     ex.a = ex.b = ex.bot = ex.top = no_cand();
     ex.nonfinite = 0;
+    if (threadIdx.x == 0) s.nLive = m;
     for (int k = threadIdx.x; k < m; k += FIN_NT) {
         const float2 q = __ldg(&src[k]);
         s.pxy[k] = q;
+        s.lst[k] = (unsigned short)k;
         if (isNode) {
             s.seg[k] = 0;
             if (__ldg(&gidx[k]) == C.idx) s.cLocal = k;
