@@ -552,6 +552,11 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
             hi_s[0] = I->level0 + K;
             continue;
         }
+        if (p.numSets == 1) {  // one set: the level is its node range
+            lo_s[r] = a;
+            hi_s[r] = b;
+            continue;
+        }
         int l = a, h = b;
         while (l < h) {
             int mid = (l + h) >> 1;
