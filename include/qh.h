@@ -170,7 +170,9 @@ qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *of
  * qh_hull2d_host -- end-to-end form of qh_hull2d_p with HOST buffers: copies
  * host_points (float[2*n]) to the device, computes, copies the hull to
  * host_out_idx (int32[n]) and the count to *host_out_count, and synchronizes
- * the stream before returning.  Pinned host memory gives the fastest copies.
+ * the stream before returning.  Entries of host_out_idx past the count are
+ * unspecified (the first min(n, 65536) entries are read back together with the
+ * count).  Pinned host memory gives the fastest copies.
  */
 qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
                          int32_t *host_out_count, qh_stream_t stream);

@@ -441,12 +441,19 @@ qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int3
     if (e != cudaSuccess) return cuda_status(e);
     qh_status st = qh_hull2d_p(plan, plan->stIn, n, plan->stOut, plan->stCnt, stream);
     if (st != QH_OK) return st;
+    // The count and the first indices come back together (one synchronisation for
+    // every hull of up to EAGER vertices); a larger hull reads the rest after.
+    constexpr long long EAGER = 65536;
+    const long long first = n < EAGER ? n : EAGER;
     e = cudaMemcpyAsync(host_out_count, plan->stCnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && first > 0)
+        e = cudaMemcpyAsync(host_out_idx, plan->stOut, sizeof(int) * (size_t)first, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     const int h = *host_out_count;
-    if (h > 0) {
-        e = cudaMemcpyAsync(host_out_idx, plan->stOut, sizeof(int) * (size_t)h, cudaMemcpyDeviceToHost, s);
+    if (h > first) {
+        e = cudaMemcpyAsync(host_out_idx + first, plan->stOut + first, sizeof(int) * (size_t)(h - first),
+                            cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_status(e);
     } else if (h < 0) {

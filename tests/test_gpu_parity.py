@@ -164,3 +164,36 @@ def test_full_batched(qh):
         a = int(off[s])
         assert np.array_equal(out[a:a + want_counts[s]], want_out[a:a + want_counts[s]]), s
     plan.close()
+
+
+def _lattice_polygon(radius: int) -> np.ndarray:
+    """Vertices of a strictly convex lattice polygon (Jarnik's construction): the
+    primitive integer vectors (a, b) with |a| + |b| <= radius, sorted by angle and
+    summed.  Consecutive edges turn by a positive angle, so every vertex is a
+    strict hull vertex; the coordinates stay integers below 2^24 (exact floats)."""
+    import math
+
+    vecs = [(a, b) for a in range(-radius, radius + 1) for b in range(-radius, radius + 1)
+            if (a or b) and abs(a) + abs(b) <= radius and math.gcd(abs(a), abs(b)) == 1]
+    vecs.sort(key=lambda v: math.atan2(v[1], v[0]))
+    pts = np.cumsum(np.array(vecs, dtype=np.int64), axis=0)
+    pts -= pts.min(axis=0)
+    assert pts.max() < 1 << 24
+    return pts.astype(np.float32)
+
+
+def test_host_buffers(qh):
+    """The host-buffer entry point: a small hull (count and indices read back
+    together) and a hull of more vertices than that first read covers."""
+    plan = qh.Plan(300_000, 1)
+    rng = np.random.default_rng(5)
+    small = rng.random((50_000, 2), dtype=np.float32)
+    assert np.array_equal(qh.hull2d_host(small, plan), oracle.hull2d(small))
+    ring = _lattice_polygon(260)                        # 82,400 strict vertices
+    c = ring.mean(axis=0)
+    inner = (c + (rng.random((100_000, 2)) - 0.5) * 1e5).astype(np.float32)  # well inside
+    pts = np.concatenate([ring, inner])[rng.permutation(len(ring) + len(inner))]
+    want = oracle.hull2d(pts)
+    assert len(want) == len(ring) > 65536
+    assert np.array_equal(qh.hull2d_host(pts, plan), want)
+    plan.close()
