@@ -517,9 +517,12 @@ __device__ __forceinline__ int status_of(unsigned err) {
 }
 
 constexpr int EMIT_NT = 256;
+constexpr int EMIT_CAP = 2048;  // segment nodes of a single set that the output pass stages in shared memory
 
 __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
     __shared__ int lo_s[MAX_LEVELS + 1], hi_s[MAX_LEVELS + 1];
+    __shared__ int kind_s[EMIT_CAP], child_s[EMIT_CAP], vc_s[EMIT_CAP];
+    __shared__ long long off_s[EMIT_CAP];
     const int i = blockIdx.x;
     if (i >= p.numSets) return;
     const unsigned err = p.ctl->err;
@@ -571,6 +574,59 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
         hi_s[r] = l2;
     }
     __syncthreads();
+    const int nN = p.ctl->levelBase[nL];
+    if (p.numSets == 1 && I->level0 == 0 && nN <= EMIT_CAP) {
+        // One set with a small tree (its nodes are 0 .. nN - 1): the same two passes
+        // over the levels, on a shared-memory copy of the tree.
+        for (int q = threadIdx.x; q < nN; q += EMIT_NT) {
+            const Node *N = &p.nodes[q];
+            const int kd = N->kind;
+            kind_s[q] = kd;
+            child_s[q] = N->child;
+            vc_s[q] = kd == K_SMALL ? 1 + N->inner : 1;
+        }
+        __syncthreads();
+        for (int r = nL - 1; r >= 0; r--) {
+            for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
+                if (kind_s[q] != K_BIG) continue;
+                const int c = child_s[q];
+                if (c >= 0 && c + 1 < nN) {
+                    vc_s[q] = vc_s[c] + vc_s[c + 1];
+                } else {
+                    set_err(p.ctl, E_INTERNAL);
+                    vc_s[q] = 0;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            long long o = 0;
+            for (int k = 0; k < K; k++) {
+                off_s[k] = o;
+                o += vc_s[k];
+            }
+            p.outCounts[i] = (int)o;
+        }
+        __syncthreads();
+        for (int r = 0; r < nL; r++) {
+            for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
+                const int kd = kind_s[q];
+                if (kd == K_BIG) {
+                    const int c = child_s[q];
+                    if (c < 0 || c + 1 >= nN) continue;
+                    off_s[c] = off_s[q];
+                    off_s[c + 1] = off_s[q] + vc_s[c];
+                } else if (off_s[q] >= 0 && off_s[q] < I->n) {
+                    p.outIdx[off + off_s[q]] = p.nodes[q].h.idx;
+                    if (kd == K_SMALL) p.nodes[q].off = off_s[q];  // where the copy pass puts its inner vertices
+                } else {
+                    set_err(p.ctl, E_INTERNAL);
+                }
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int r = nL - 1; r >= 0; r--) {
         for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
             Node *N = &p.nodes[q];
