@@ -38,7 +38,6 @@ struct FinSmem {
     unsigned short best[2 * FM];
     unsigned short newId[2 * FM];
     int scan[FIN_NT / 32 + 1];
-    long long scan64[FIN_NT / 32 + 1];
     int ticket, cLocal, nOrd, S, K, degenerate, nonfinite, nLive;
     long long liveCount;
     unsigned short poly[4];
@@ -207,84 +206,41 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
         }
     }
     __syncthreads();
-    // children that hold points become the new live segments
+    // children that hold points become the new live segments (one scan of the
+    // packed per-thread counts: live children in the high half, their points in
+    // the low half; both totals stay below 2^16)
     {
         const int per = (nch + FIN_NT - 1) / FIN_NT;
         const int b = min(nch, (int)threadIdx.x * per), e = min(nch, b + per);
-        int has = 0;
-        long long pts = 0;
+        int packed = 0;
         for (int c = b; c < e; c++) {
             const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
-            has += cnt > 0u;
-            pts += cnt;
+            packed += (cnt > 0u ? 1 << 16 : 0) + (int)cnt;
         }
         int tot;
-        int x = block_excl_scan<int, FIN_NT>(has, s.scan, tot);
+        int x = block_excl_scan<int, FIN_NT>(packed, s.scan, tot) >> 16;
         for (int c = b; c < e; c++) {
             const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
             s.newId[c] = cnt > 0u ? (unsigned short)(x++) : NONE16;
         }
-        long long ptot;
-        block_excl_scan<long long, FIN_NT>(pts, reinterpret_cast<long long *>(s.scan64), ptot);
         if (threadIdx.x == 0) {
-            s.S = tot;
-            s.liveCount = ptot;
+            s.S = tot >> 16;
+            s.liveCount = tot & 0xffff;
         }
     }
     __syncthreads();
-    // new CCW list of heads
-    if (initial) {
-        for (int c = threadIdx.x; c < s.K; c += FIN_NT) {
-            OrdE o;
-            o.head = s.poly[c];
-            o.live = s.newId[c];
-            o.c = o.live != NONE16 ? s.best[c] : NONE16;
-            o.pad = 0;
-            ordN[c] = o;
-            if (o.live != NONE16) s.lpos[o.live] = (unsigned short)c;
-        }
-        if (threadIdx.x == 0) s.nOrd = s.K;
-    } else {
-        const int per = (nOrd + FIN_NT - 1) / FIN_NT;
-        const int b = min(nOrd, (int)threadIdx.x * per), e = min(nOrd, b + per);
-        int w = 0;
-        for (int q = b; q < e; q++) w += ord[q].live != NONE16 ? 2 : 1;
-        int tot;
-        int np = block_excl_scan<int, FIN_NT>(w, s.scan, tot);
-        if (tot > FM + 4) {  // guard: at most one head per point plus the chord ends
-            if (threadIdx.x == 0) {
-                set_err(p.ctl, E_INTERNAL);
-                s.S = 0;
-                s.nOrd = 0;
-            }
-            __syncthreads();
-            return;
-        }
-        for (int q = b; q < e; q++) {
-            const OrdE o = ord[q];
-            if (o.live == NONE16) {
-                ordN[np++] = o;
-                continue;
-            }
-            const int j = o.live;
-            for (int wch = 0; wch < 2; wch++) {
-                OrdE n;
-                n.head = wch ? o.c : o.head;
-                n.live = s.newId[2 * j + wch];
-                n.c = n.live != NONE16 ? s.best[2 * j + wch] : NONE16;
-                n.pad = 0;
-                ordN[np] = n;
-                if (n.live != NONE16) s.lpos[n.live] = (unsigned short)np;
-                np++;
-            }
-        }
-        if (threadIdx.x == 0) s.nOrd = tot;
-    }
-    __syncthreads();
-    // relabel the points with their new live segment and keep the live ones
-    // in the list (a contiguous range of at most FIN_PER entries per thread,
-    // read before the scan's barriers and rewritten after them)
+    // The new CCW list of heads and the relabelled, compacted list of live
+    // points, with one scan of the packed per-thread sizes (list entries in the
+    // high half, live points in the low half).  Each thread reads its ranges
+    // (at most FIN_PER points) before the scan's barriers and writes after them.
     {
+        int w = 0, bo = 0, eo = 0;
+        if (!initial) {
+            const int per = (nOrd + FIN_NT - 1) / FIN_NT;
+            bo = min(nOrd, (int)threadIdx.x * per);
+            eo = min(nOrd, bo + per);
+            for (int q = bo; q < eo; q++) w += ord[q].live != NONE16 ? 2 : 1;
+        }
         const int b = min(nL, (int)threadIdx.x * FIN_PER), e = min(nL, b + FIN_PER);
         unsigned short keep[FIN_PER];
         unsigned km = 0u;
@@ -301,11 +257,55 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
             }
         }
         int tot;
-        int x = block_excl_scan<int, FIN_NT>(__popc(km), s.scan, tot);
+        const int x = block_excl_scan<int, FIN_NT>((w << 16) + __popc(km), s.scan, tot);
+        if (!initial && (tot >> 16) > FM + 4) {  // guard: at most one head per point plus the chord ends
+            if (threadIdx.x == 0) {
+                set_err(p.ctl, E_INTERNAL);
+                s.S = 0;
+                s.nOrd = 0;
+            }
+            __syncthreads();
+            return;
+        }
+        int xl = x & 0xffff;
 #pragma unroll
         for (int j = 0; j < FIN_PER; j++)
-            if ((km >> j) & 1u) s.lst[x++] = keep[j];
-        if (threadIdx.x == 0) s.nLive = tot;
+            if ((km >> j) & 1u) s.lst[xl++] = keep[j];
+        if (initial) {
+            for (int c = threadIdx.x; c < s.K; c += FIN_NT) {
+                OrdE o;
+                o.head = s.poly[c];
+                o.live = s.newId[c];
+                o.c = o.live != NONE16 ? s.best[c] : NONE16;
+                o.pad = 0;
+                ordN[c] = o;
+                if (o.live != NONE16) s.lpos[o.live] = (unsigned short)c;
+            }
+        } else {
+            int np = x >> 16;
+            for (int q = bo; q < eo; q++) {
+                const OrdE o = ord[q];
+                if (o.live == NONE16) {
+                    ordN[np++] = o;
+                    continue;
+                }
+                const int j = o.live;
+                for (int wch = 0; wch < 2; wch++) {
+                    OrdE n;
+                    n.head = wch ? o.c : o.head;
+                    n.live = s.newId[2 * j + wch];
+                    n.c = n.live != NONE16 ? s.best[2 * j + wch] : NONE16;
+                    n.pad = 0;
+                    ordN[np] = n;
+                    if (n.live != NONE16) s.lpos[n.live] = (unsigned short)np;
+                    np++;
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            s.nOrd = initial ? s.K : (tot >> 16);
+            s.nLive = tot & 0xffff;
+        }
     }
     if (threadIdx.x == 0)
         atomicAdd((unsigned long long *)&p.ctl->live[min(gen, MAX_GEN - 1)], (unsigned long long)s.liveCount);
