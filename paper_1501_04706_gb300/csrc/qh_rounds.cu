@@ -592,9 +592,6 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
         merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
 #ifdef QH_PROFILE
         if (threadIdx.x == 0) atomicMax(&p.ctl->prof[30], global_ns() - tm0);
-        const unsigned long long tm1 = global_ns();
-        merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);  // again, warm
-        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[32], global_ns() - tm1);
 #endif
         if (threadIdx.x < nslot) {
             Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
