@@ -197,3 +197,43 @@ def test_host_buffers(qh):
     assert len(want) == len(ring) > 65536
     assert np.array_equal(qh.hull2d_host(pts, plan), want)
     plan.close()
+
+
+def test_batched_degenerate_sets(qh):
+    """One batched call over sets of every kind the front end classifies: empty, a
+    single point, equal points (small and tiled), a tiled collinear line, a circle,
+    a strictly convex lattice polygon, and big sets next to tiny ones."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    t = np.linspace(-1, 1, 20_001).astype(np.float32)
+    ring = _lattice_polygon(60)
+    ang = rng.random(6000) * 2 * np.pi
+    sets = [
+        np.zeros((0, 2), np.float32),
+        np.array([[0.25, -0.5]], np.float32),
+        np.full((5, 2), 2.0, np.float32),
+        np.full((10_000, 2), -1.5, np.float32),                                 # tiled, all equal
+        np.stack([t, np.float32(0.5) * t], 1)[rng.permutation(len(t))],       # tiled, collinear
+        np.zeros((0, 2), np.float32),
+        np.stack([np.cos(ang), np.sin(ang)], 1).astype(np.float32),           # circle
+        ring[rng.permutation(len(ring))],                                      # every point a vertex
+        synth.disk(100_000, seed=3),
+        np.array([[0, 0], [1, 0], [0, 1]], np.float32),
+        rng.random((4097, 2), dtype=np.float32),
+    ]
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    p = np.concatenate(sets).astype(np.float32)
+    plan = qh.Plan(len(p), len(sets))
+    out, counts = qh.hull2d_batched(_dev(p), torch.from_numpy(off).cuda(), plan)
+    out = out.cpu().numpy()
+    counts = counts.cpu().numpy()
+    want_out, want_counts = oracle.hull2d_batched(p, off)
+    assert np.array_equal(counts, want_counts)
+    assert want_counts[0] == 0 and want_counts[1] == 1 and want_counts[3] == 1 and want_counts[4] == 2
+    assert want_counts[7] == len(ring)
+    for s in range(len(sets)):
+        a = int(off[s])
+        assert np.array_equal(out[a:a + counts[s]], want_out[a:a + counts[s]]), s
+    plan.close()
