@@ -224,6 +224,15 @@ qh_status qh_check_orient_device(const float *tri, int64_t n, int32_t prec, int3
 qh_status qh_check_dist_host(const float *quads, int64_t n, int32_t *sign);
 qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_stream_t stream);
 
+/*
+ * qh_debug_prof_cta -- profiling hook: copies the first n (at most 1024) rows of
+ * eight uint64 words of the grid-wide kernel's per-CTA records (initial-split
+ * loop times and counts, and the phase timeline) to the host buffer host.  The
+ * records exist only in a library built with -DQH_PROFILE (256-thread variant);
+ * elsewhere it returns -1 and copies nothing.  Returns 0 on success.
+ */
+int qh_debug_prof_cta(void *host, int n);
+
 #ifdef __cplusplus
 }
 #endif

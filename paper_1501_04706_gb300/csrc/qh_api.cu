@@ -551,7 +551,5 @@ qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_
 
 }  // extern "C"
 
-#ifdef QH_PROFILE
-// Profiling builds only: per-CTA records of the initial split (8 x uint64 per CTA).
+// Per-CTA records of the grid-wide kernel (profiling builds; -1 in the others).
 extern "C" int qh_debug_prof_cta(void *host, int n) { return qh::v256::prof_cta_copy(host, n); }
-#endif
