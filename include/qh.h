@@ -56,7 +56,10 @@ typedef enum {
 #define QH_PREC_F32 0x0u    /* FP32 predicates with certified bound + exact fallback */
 #define QH_PREC_F64 0x2u    /* plain FP64 predicates with bound + the same exact fallback */
 
-#define QH_MAX_GEN 64
+#define QH_MAX_GEN 512
+
+/* Largest plan (points): int32 indices, two nested copies of the points, up to 2n tree nodes. */
+#define QH_MAX_PLAN_POINTS (1ll << 29)
 
 typedef struct qh_plan_s *qh_plan;
 
@@ -67,14 +70,15 @@ typedef struct {
     int32_t small_problems;     /* segments and sets finished by one thread block each */
     int32_t nodes;              /* segments created by grid-wide rounds */
     int32_t big_sets;           /* point sets that took the grid-wide path */
-    int64_t live[QH_MAX_GEN];   /* points held by segments after each generation (all sets) */
+    int32_t levels;             /* levels of the segment tree (initial segments = level 0) */
+    int32_t pad0;
+    int64_t live[QH_MAX_GEN];   /* points held by segments after each generation (all sets);
+                                   generations past the last entry add to it */
     int64_t exact_orient;       /* orientation tests decided by the exact fallback */
     int64_t exact_compare;      /* farthest-point comparisons decided by the exact fallback */
     float phase_ms[5];          /* with timing on: grid rounds, finisher, emit, copy, total */
     float grid_phase_us[16];    /* inside the grid-wide kernel: set prep, extreme points, initial
                                    split, then grid-wide rounds 1.. (device clock) */
-    uint64_t section_cycles[48];/* per-tile section cycle sums of CTA thread 0; zero unless the
-                                   library was built with -DQH_PROFILE */
     int64_t grid_points;        /* points of the sets tiled by the grid-wide kernel (read twice:
                                    extreme points and initial split) */
     int64_t grid_read;          /* live points read by grid-wide rounds after the initial split */
@@ -85,8 +89,12 @@ typedef struct {
 /*
  * qh_plan_create -- allocate a plan for up to max_points points in up to
  * max_sets sets.  flags: QH_MODE_* | QH_PREC_*.  The plan holds roughly
- * 64 bytes of device scratch per point.  Errors: QH_ERR_INVALID_ARG (sizes < 1),
- * QH_ERR_OOM, QH_ERR_CUDA.
+ * 120 bytes of device scratch per point: two nested copies of the live points,
+ * and a segment tree, small-segment queue and level table sized for any input
+ * (a set of n points has at most 2n tree nodes, n small segments and n levels),
+ * so no input within max_points exceeds it, however deep the recursion.
+ * Errors: QH_ERR_INVALID_ARG (sizes < 1), QH_ERR_CAPACITY (max_points above
+ * QH_MAX_PLAN_POINTS), QH_ERR_OOM, QH_ERR_CUDA.
  */
 qh_status qh_plan_create(int64_t max_points, int32_t max_sets, uint32_t flags, qh_plan *out);
 
@@ -112,6 +120,15 @@ qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int3
  * (Not in the paper: its kernels are Thrust calls with library-chosen launch shapes.)
  */
 qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block);
+
+/*
+ * Debug limits for tests of the device-side error paths (not in the paper).  spin_limit: polls (each
+ * followed by a ~100 ns sleep) before a grid-barrier wait gives up with QH_ERR_TIMEOUT; 0 restores the
+ * default (2^22).  max_tree_nodes: lowers the segment-tree capacity so that a deep enough input reports
+ * QH_ERR_CAPACITY; 0 restores the full table.  Both errors reach the output counts as -status, the
+ * kernels leave at their next barrier, and the plan works normally again once the limits are reset.
+ */
+qh_status qh_plan_set_debug(qh_plan plan, uint32_t spin_limit, int32_t max_tree_nodes);
 
 /* The plan's current tuning: block size, points per thread, small-segment cutover, grid CTAs per SM. */
 qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *items_per_thread,
@@ -187,10 +204,12 @@ qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int3
  *   points, n, out_idx, out_count, stream: as for qh_hull2d_p.
  *   n must not exceed QH_NOALLOC_MAX_POINTS; larger sets return QH_ERR_CAPACITY
  *   without touching the device.
- * Scratch: one fixed array in the library's device image (about 16 MB on every
+ * Scratch: one fixed array in the library's device image (about 31 MB on every
  * GPU that loads the library, held until the process exits); no cudaMalloc,
  * cudaFree or other allocating call is made.  The first call on a device looks up
- * the array's address for that device (it must come before any stream capture).
+ * the array's address for that device (it must come before any stream capture)
+ * and keeps it for the life of the process: a cudaDeviceReset after that first
+ * call invalidates the kept address and is not supported.
  * All calls share the array: calls that overlap on the GPU (other streams, other
  * host threads) race and corrupt each other's results; serialise them.
  */
@@ -224,14 +243,6 @@ qh_status qh_check_orient_device(const float *tri, int64_t n, int32_t prec, int3
 qh_status qh_check_dist_host(const float *quads, int64_t n, int32_t *sign);
 qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_stream_t stream);
 
-/*
- * qh_debug_prof_cta -- profiling hook: copies the first n (at most 1024) rows of
- * eight uint64 words of the grid-wide kernel's per-CTA records (initial-split
- * loop times and counts, and the phase timeline) to the host buffer host.  The
- * records exist only in a library built with -DQH_PROFILE (256-thread variant);
- * elsewhere it returns -1 and copies nothing.  Returns 0 on success.
- */
-int qh_debug_prof_cta(void *host, int n);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ __all__ = [
 
 MODE_QUAD, MODE_CHORD = 0x0, 0x1
 PREC_F32, PREC_F64 = 0x0, 0x2
-MAX_GEN = 64
+MAX_GEN = 512
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "non-finite input coordinate", 3: "CUDA runtime error",
           4: "out of device memory", 5: "capacity exceeded", 6: "device-side wait timed out",
@@ -43,11 +43,10 @@ class QhError(RuntimeError):
 class _Stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_int32), ("global_rounds", ctypes.c_int32),
                 ("generations", ctypes.c_int32), ("small_problems", ctypes.c_int32),
-                ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32),
-                ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
+                ("nodes", ctypes.c_int32), ("big_sets", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("live", ctypes.c_int64 * MAX_GEN), ("exact_orient", ctypes.c_int64),
                 ("exact_compare", ctypes.c_int64), ("phase_ms", ctypes.c_float * 5),
-                ("grid_phase_us", ctypes.c_float * 16), ("section_cycles", ctypes.c_uint64 * 48),
-                ("grid_points", ctypes.c_int64), ("grid_read", ctypes.c_int64), ("grid_written", ctypes.c_int64),
+                ("grid_phase_us", ctypes.c_float * 16), ("grid_points", ctypes.c_int64), ("grid_read", ctypes.c_int64), ("grid_written", ctypes.c_int64),
                 ("small_points", ctypes.c_int64)]
 
 
@@ -68,6 +67,8 @@ def load() -> ctypes.CDLL:
     lib.qh_plan_set_flags.argtypes = [vp, u32]
     lib.qh_plan_set_tuning.argtypes = [vp, i32, i32, i32]
     lib.qh_plan_set_block.argtypes = [vp, i32]
+    lib.qh_plan_set_debug.argtypes = [vp, u32, i32]
+    lib.qh_hull2d_noalloc.argtypes = [vp, i64, vp, vp, vp]
     lib.qh_plan_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32)]
     lib.qh_plan_autotune.argtypes = [vp, vp, vp, i32, i64, vp, vp, i32, vp]
@@ -84,6 +85,7 @@ def load() -> ctypes.CDLL:
     lib.qh_check_dist_host.argtypes = [vp, i64, vp]
     lib.qh_check_dist_device.argtypes = [vp, i64, vp, vp]
     for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_plan_set_block",
+              "qh_plan_set_debug", "qh_hull2d_noalloc",
               "qh_plan_get_tuning", "qh_plan_autotune", "qh_hull2d_p",
               "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_plan_get_stats", "qh_check_orient_host",
               "qh_check_orient_device", "qh_check_dist_host", "qh_check_dist_device"):
@@ -136,6 +138,11 @@ class Plan:
         """Block size of the grid-wide kernel: 256 or 128 threads (16 points per thread)."""
         _check(load().qh_plan_set_block(self.handle, int(threads)), "qh_plan_set_block")
 
+    def set_debug(self, spin_limit: int = 0, max_tree_nodes: int = 0) -> None:
+        """Debug limits for the device-side error paths (0 = default): grid-barrier polls before a
+        wait gives up (QH_ERR_TIMEOUT) and the segment-tree capacity (QH_ERR_CAPACITY)."""
+        _check(load().qh_plan_set_debug(self.handle, int(spin_limit), int(max_tree_nodes)), "qh_plan_set_debug")
+
     def tuning(self) -> dict:
         v = [ctypes.c_int32() for _ in range(4)]
         _check(load().qh_plan_get_tuning(self.handle, *[ctypes.byref(x) for x in v]), "qh_plan_get_tuning")
@@ -166,11 +173,10 @@ class Plan:
         _check(load().qh_plan_get_stats(self.handle, ctypes.byref(s)), "qh_plan_get_stats")
         g = s.generations
         return {"device_status": s.device_status, "global_rounds": s.global_rounds, "generations": g,
-                "small_problems": s.small_problems, "nodes": s.nodes, "big_sets": s.big_sets,
+                "small_problems": s.small_problems, "nodes": s.nodes, "big_sets": s.big_sets, "levels": s.levels,
                 "live": [int(v) for v in s.live[: min(g, MAX_GEN)]], "exact_orient": int(s.exact_orient),
                 "exact_compare": int(s.exact_compare), "phase_ms": [float(v) for v in s.phase_ms],
-                "grid_phase_us": [float(v) for v in s.grid_phase_us if v > 0],
-                "section_cycles": [int(v) for v in s.section_cycles], "grid_points": int(s.grid_points),
+                "grid_phase_us": [float(v) for v in s.grid_phase_us if v > 0], "grid_points": int(s.grid_points),
                 "grid_read": int(s.grid_read), "grid_written": int(s.grid_written),
                 "small_points": int(s.small_points)}
 

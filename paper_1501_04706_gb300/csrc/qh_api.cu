@@ -32,13 +32,21 @@ struct qh_plan_s {
     Inst *inst = nullptr;
     int *bigInst = nullptr, *smallInst = nullptr;
     long long *bigTilePrefix = nullptr;
-    Node *nodes = nullptr;
-    int maxNodes = 0;
+    Node *nodes = nullptr;  // ring of two levels
+    int slotCap = 0;
+    TNode *tnodes = nullptr;
+    int maxTNodes = 0;
+    int *levelBase = nullptr;
+    int maxLevels = 0;
+    SmallRec *small = nullptr;
+    int maxSmall = 0;
     int *bigList[2] = {nullptr, nullptr};
     long long *vstart[2] = {nullptr, nullptr};
     int maxBig = 0;
-    int *smallQ = nullptr;
     Ctl *ctl = nullptr;
+    // debug limits (0: defaults)
+    unsigned dbgSpin = 0;
+    int dbgTNodes = 0;
     // host side
     Ctl *hctl = nullptr;  // pinned
     cudaStream_t last = nullptr;
@@ -79,11 +87,13 @@ void plan_free(qh_plan p) {
     cudaFree(p->smallInst);
     cudaFree(p->bigTilePrefix);
     cudaFree(p->nodes);
+    cudaFree(p->tnodes);
+    cudaFree(p->levelBase);
+    cudaFree(p->small);
     cudaFree(p->bigList[0]);
     cudaFree(p->bigList[1]);
     cudaFree(p->vstart[0]);
     cudaFree(p->vstart[1]);
-    cudaFree(p->smallQ);
     cudaFree(p->ctl);
     cudaFree(p->stIn);
     cudaFree(p->stOut);
@@ -114,19 +124,31 @@ qh_status plan_alloc(qh_plan p) {
     QH_ALLOC(p->bigInst, p->maxSets + 1);
     QH_ALLOC(p->smallInst, p->maxSets + 1);
     QH_ALLOC(p->bigTilePrefix, p->maxSets + 2);
-    // every big segment holds more than a tile of points (the smallest tile of the variants)
+    // Every big segment holds more than a tile of points (the smallest tile of
+    // the variants), so a level has at most N / TILE_MIN of them.
     p->maxBig = (int)(N / TILE_MIN + 16);
-    long long bigSets = N / FIN_MAX + 1;
+    long long bigSets = N / (FIN_MAX + 1) + 1;
     if (bigSets > p->maxSets) bigSets = p->maxSets;
-    long long nodes = 4 * bigSets + 16ll * 2 * p->maxBig + 4096;
-    if (nodes > 0x7fffffffll) nodes = 0x7fffffffll;
-    p->maxNodes = (int)nodes;
-    QH_ALLOC(p->nodes, p->maxNodes);
+    // Ring slot: the K <= 4 initial segments of every big set, or the two
+    // children of every big segment of a level.
+    const long long slot = (4 * bigSets > 2ll * p->maxBig ? 4 * bigSets : 2ll * p->maxBig) + 16;
+    p->slotCap = (int)slot;
+    QH_ALLOC(p->nodes, 2 * slot);
+    // Segment tree: every node's head is a distinct hull vertex of its set, so
+    // a set of n points has at most n leaves and n - 1 split segments; a split
+    // segment loses at least its farthest point, so there are fewer than N
+    // levels; every small segment holds a point.  No input of at most N points
+    // exceeds these tables.
+    p->maxTNodes = (int)(2 * N + 64);
+    p->maxLevels = (int)(N + 2);
+    p->maxSmall = (int)(N + 64);
+    QH_ALLOC(p->tnodes, p->maxTNodes);
+    QH_ALLOC(p->levelBase, p->maxLevels + 2);
+    QH_ALLOC(p->small, p->maxSmall);
     QH_ALLOC(p->bigList[0], p->maxBig + 1);
     QH_ALLOC(p->bigList[1], p->maxBig + 1);
     QH_ALLOC(p->vstart[0], p->maxBig + 2);
     QH_ALLOC(p->vstart[1], p->maxBig + 2);
-    QH_ALLOC(p->smallQ, p->maxNodes);
     QH_ALLOC(p->ctl, 1);
 #undef QH_ALLOC
     e = cudaMallocHost((void **)&p->hctl, sizeof(Ctl));
@@ -166,9 +188,15 @@ Params make_params(qh_plan pl, const float *points, const long long *offsets, lo
     p.smallInst = pl->smallInst;
     p.bigTilePrefix = pl->bigTilePrefix;
     p.nodes = pl->nodes;
-    p.maxNodes = pl->maxNodes;
+    p.slotCap = pl->slotCap;
+    p.tnodes = pl->tnodes;
+    p.maxTNodes = pl->dbgTNodes > 0 && pl->dbgTNodes < pl->maxTNodes ? pl->dbgTNodes : pl->maxTNodes;
+    p.levelBase = pl->levelBase;
+    p.maxLevels = pl->maxLevels;
+    p.small = pl->small;
+    p.maxSmall = pl->maxSmall;
+    p.spinLimit = pl->dbgSpin > 0 ? pl->dbgSpin : SPIN_LIMIT;
     p.maxBig = pl->maxBig;
-    p.smallQ = pl->smallQ;
     p.ctl = pl->ctl;
     p.cut = pl->cut;
     return p;
@@ -239,7 +267,7 @@ const char *qh_status_string(qh_status s) {
 
 qh_status qh_plan_create(int64_t max_points, int32_t max_sets, uint32_t flags, qh_plan *out) {
     if (!out || max_points < 1 || max_sets < 1 || (flags & ~3u)) return QH_ERR_INVALID_ARG;
-    if (max_points > (1ll << 30)) return QH_ERR_CAPACITY;  // indices are int32, nested ranges 2x
+    if (max_points > QH_MAX_PLAN_POINTS) return QH_ERR_CAPACITY;  // int32 indices, nested ranges 2x, tree 2x
     *out = nullptr;
     qh_plan p = new (std::nothrow) qh_plan_s();
     if (!p) return QH_ERR_OOM;
@@ -294,6 +322,13 @@ qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block) {
             return QH_OK;
         }
     return QH_ERR_INVALID_ARG;
+}
+
+qh_status qh_plan_set_debug(qh_plan plan, uint32_t spin_limit, int32_t max_tree_nodes) {
+    if (!plan || max_tree_nodes < 0) return QH_ERR_INVALID_ARG;
+    plan->dbgSpin = spin_limit;
+    plan->dbgTNodes = max_tree_nodes;
+    return QH_OK;
 }
 
 qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *items_per_thread, int32_t *cutover,
@@ -482,7 +517,7 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
         if (c.live[g] > 0) last = g;
     }
     out->generations = last < 0 ? 1 : last + 2;
-    for (int k = 0; k < 48; k++) out->section_cycles[k] = c.prof[k];
+    out->levels = c.nLevels;
     out->exact_orient = (int64_t)c.exactOrient;
     out->grid_points = c.bigPoints;
     out->grid_read = c.gridRead;
@@ -491,7 +526,7 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
     out->exact_compare = (int64_t)c.exactCmp;
     for (int k = 0; k < 16; k++) {
         const int hi = k + 1;
-        if (hi >= MAX_LEVELS + 4 || c.tphase[hi] == 0ull || c.tphase[k] == 0ull) break;
+        if (hi >= MAX_STAMPS || c.tphase[hi] == 0ull || c.tphase[k] == 0ull) break;
         out->grid_phase_us[k] = (float)((double)(c.tphase[hi] - c.tphase[k]) * 1e-3);
     }
     if (plan->evRecorded) {
@@ -550,6 +585,3 @@ qh_status qh_check_dist_device(const float *quads, int64_t n, int32_t *sign, qh_
 }
 
 }  // extern "C"
-
-// Per-CTA records of the grid-wide kernel (profiling builds; -1 in the others).
-extern "C" int qh_debug_prof_cta(void *host, int n) { return qh::v256::prof_cta_copy(host, n); }

@@ -324,18 +324,22 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     int gen = 0;
     Cand H = no_cand(), E = no_cand(), C = no_cand();
     long long pstart = 0;
+    int tree = -1;
     if (isNode) {
-        const Node *N = &p.nodes[id];
-        m = N->count;
+        const SmallRec *R = &p.small[id];
+        m = R->count;
         if (threadIdx.x == 0) atomicAdd((unsigned long long *)&p.ctl->smallPoints, (unsigned long long)m);
-        const int buf = N->buf;
-        pstart = N->pstart;
-        src = p.xy[buf] + pstart;
-        gidx = p.id[buf] + pstart;
-        gen = N->level + 1;
-        H = N->h;
-        E = N->e;
-        C = N->c;
+        const int level = R->level;
+        const long long setOff = p.inst[R->inst].off;
+        pstart = R->pstart;
+        src = p.xy[level & 1] + pstart;  // level r was written by round r into buffer r & 1
+        gidx = p.id[level & 1] + pstart;
+        gen = level + 1;
+        tree = R->tree;
+        const float2 hp = __ldg(&p.pts[setOff + R->hIdx]), ep = __ldg(&p.pts[setOff + R->eIdx]);
+        H = mk_cand(hp.x, hp.y, R->hIdx);
+        E = mk_cand(ep.x, ep.y, R->eIdx);
+        C.idx = R->cIdx;
     } else {
         const Inst *I = &p.inst[id];
         m = (int)I->n;
@@ -470,7 +474,10 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     if (isNode) {
         // heads strictly between h (entry 0) and e (last entry)
         for (int q = 1 + threadIdx.x; q < nOrd - 1; q += FIN_NT) p.vscratch[pstart + q - 1] = __ldg(&gidx[ord[q].head]);
-        if (threadIdx.x == 0) p.nodes[id].inner = nOrd - 2;
+        if (threadIdx.x == 0) {
+            p.small[id].cIdx = nOrd - 2;     // inner vertices, for the copy pass
+            p.tnodes[tree].val = nOrd - 1;   // the leaf's vertices: its head and the inner ones
+        }
     } else {
         for (int q = threadIdx.x; q < nOrd; q += FIN_NT) p.outIdx[outOff + q] = ord[q].head;
         if (threadIdx.x == 0) p.outCounts[id] = nOrd;
@@ -493,7 +500,7 @@ template <typename P> __global__ void __launch_bounds__(FIN_NT, 1) finish_kernel
         if (w < nSI)
             fin_solve<P>(p, s, false, p.smallInst[w], exact_o, exact_c);
         else
-            fin_solve<P>(p, s, true, p.smallQ[w - nSI], exact_o, exact_c);
+            fin_solve<P>(p, s, true, w - nSI, exact_o, exact_c);
     }
     unsigned long long eo = (unsigned long long)exact_o, ec = (unsigned long long)exact_c;
     for (int d = 16; d >= 1; d >>= 1) {
@@ -517,12 +524,44 @@ __device__ __forceinline__ int status_of(unsigned err) {
 }
 
 constexpr int EMIT_NT = 256;
-constexpr int EMIT_CAP = 2048;  // segment nodes of a single set that the output pass stages in shared memory
+constexpr int EMIT_CAP = 2048;  // tree nodes of a single set that the output pass stages in shared memory
 
+// Nodes of set i in level r of the segment tree: [lo, hi).
+__device__ __forceinline__ void set_level_range(const Params &p, const Inst *I, int i, int K, int r, int &lo,
+                                                int &hi) {
+    if (r == 0) {
+        lo = I->level0;
+        hi = lo + K;
+        return;
+    }
+    const int a = __ldcg(&p.levelBase[r]), b = __ldcg(&p.levelBase[r + 1]);
+    if (p.numSets == 1) {  // one set: the level is its node range
+        lo = a;
+        hi = b;
+        return;
+    }
+    int l = a, h = b;
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (__ldcg(&p.tnodes[mid].inst) < i) l = mid + 1; else h = mid;
+    }
+    int l2 = l, h2 = b;
+    while (l2 < h2) {
+        const int mid = (l2 + h2) >> 1;
+        if (__ldcg(&p.tnodes[mid].inst) <= i) l2 = mid + 1; else h2 = mid;
+    }
+    lo = l;
+    hi = l2;
+}
+
+// One block per set.  Bottom-up over the levels of the segment tree, every
+// split segment's vertex count is the sum of its children's; top-down, the
+// children of a segment at output offset o start at o and o + (vertices of
+// the first child), and every leaf writes its head at its offset (the copy
+// pass adds the inner vertices of small segments after it).  The levels live
+// in global memory, so the tree may be of any depth.
 __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
-    __shared__ int lo_s[MAX_LEVELS + 1], hi_s[MAX_LEVELS + 1];
-    __shared__ int kind_s[EMIT_CAP], child_s[EMIT_CAP], vc_s[EMIT_CAP];
-    __shared__ long long off_s[EMIT_CAP];
+    __shared__ int child_s[EMIT_CAP], val_s[EMIT_CAP], head_s[EMIT_CAP];
     const int i = blockIdx.x;
     if (i >= p.numSets) return;
     const unsigned err = p.ctl->err;
@@ -537,7 +576,7 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
         if (threadIdx.x == 0) p.outCounts[i] = -2;
         return;
     }
-    const long long off = I->off;
+    const long long off = I->off, n = I->n;
     if (kind == I_DEGEN) {
         if (threadIdx.x == 0) {
             p.outIdx[off] = I->poly[0].idx;
@@ -547,78 +586,55 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
     }
     const int nL = p.ctl->nLevels;
     const int K = I->K;
-    // node range of this set in every level (levels are grouped by set, in set order)
-    for (int r = threadIdx.x; r < nL; r += EMIT_NT) {
-        const int a = p.ctl->levelBase[r], b = p.ctl->levelBase[r + 1];
-        if (r == 0) {
-            lo_s[0] = I->level0;
-            hi_s[0] = I->level0 + K;
-            continue;
-        }
-        if (p.numSets == 1) {  // one set: the level is its node range
-            lo_s[r] = a;
-            hi_s[r] = b;
-            continue;
-        }
-        int l = a, h = b;
-        while (l < h) {
-            int mid = (l + h) >> 1;
-            if (p.nodes[mid].inst < i) l = mid + 1; else h = mid;
-        }
-        int l2 = l, h2 = b;
-        while (l2 < h2) {
-            int mid = (l2 + h2) >> 1;
-            if (p.nodes[mid].inst <= i) l2 = mid + 1; else h2 = mid;
-        }
-        lo_s[r] = l;
-        hi_s[r] = l2;
-    }
-    __syncthreads();
-    const int nN = p.ctl->levelBase[nL];
+    const int nN = __ldcg(&p.levelBase[nL]);
     if (p.numSets == 1 && I->level0 == 0 && nN <= EMIT_CAP) {
-        // One set with a small tree (its nodes are 0 .. nN - 1): the same two passes
-        // over the levels, on a shared-memory copy of the tree.
+        // One set with a small tree (its nodes are 0 .. nN - 1): the same two
+        // passes on a shared-memory copy of the tree.
         for (int q = threadIdx.x; q < nN; q += EMIT_NT) {
-            const Node *N = &p.nodes[q];
-            const int kd = N->kind;
-            kind_s[q] = kd;
-            child_s[q] = N->child;
-            vc_s[q] = kd == K_SMALL ? 1 + N->inner : 1;
+            const int4 t = __ldcg(reinterpret_cast<const int4 *>(&p.tnodes[q]));
+            child_s[q] = t.x;
+            head_s[q] = t.y;
+            val_s[q] = t.z;
         }
         __syncthreads();
         for (int r = nL - 1; r >= 0; r--) {
-            for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
-                if (kind_s[q] != K_BIG) continue;
+            int lo, hi;
+            set_level_range(p, I, i, K, r, lo, hi);
+            for (int q = lo + threadIdx.x; q < hi; q += EMIT_NT) {
                 const int c = child_s[q];
-                if (c >= 0 && c + 1 < nN) {
-                    vc_s[q] = vc_s[c] + vc_s[c + 1];
+                if (c < 0) continue;
+                if (c + 1 < nN) {
+                    val_s[q] = val_s[c] + val_s[c + 1];
                 } else {
                     set_err(p.ctl, E_INTERNAL);
-                    vc_s[q] = 0;
+                    val_s[q] = 0;
                 }
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            long long o = 0;
+            int o = 0;
             for (int k = 0; k < K; k++) {
-                off_s[k] = o;
-                o += vc_s[k];
+                const int v = val_s[k];
+                val_s[k] = o;
+                o += v;
             }
-            p.outCounts[i] = (int)o;
+            p.outCounts[i] = o;
         }
         __syncthreads();
         for (int r = 0; r < nL; r++) {
-            for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
-                const int kd = kind_s[q];
-                if (kd == K_BIG) {
-                    const int c = child_s[q];
-                    if (c < 0 || c + 1 >= nN) continue;
-                    off_s[c] = off_s[q];
-                    off_s[c + 1] = off_s[q] + vc_s[c];
-                } else if (off_s[q] >= 0 && off_s[q] < I->n) {
-                    p.outIdx[off + off_s[q]] = p.nodes[q].h.idx;
-                    if (kd == K_SMALL) p.nodes[q].off = off_s[q];  // where the copy pass puts its inner vertices
+            int lo, hi;
+            set_level_range(p, I, i, K, r, lo, hi);
+            for (int q = lo + threadIdx.x; q < hi; q += EMIT_NT) {
+                const int c = child_s[q], o = val_s[q];
+                if (c >= 0) {
+                    if (c + 1 >= nN) continue;
+                    const int a = val_s[c];
+                    val_s[c] = o;
+                    val_s[c + 1] = o + a;
+                } else if (o >= 0 && o < n) {
+                    p.outIdx[off + o] = head_s[q];
+                    p.tnodes[q].val = o;  // where the copy pass puts a small segment's inner vertices
                 } else {
                     set_err(p.ctl, E_INTERNAL);
                 }
@@ -628,64 +644,71 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
         return;
     }
     for (int r = nL - 1; r >= 0; r--) {
-        for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
-            Node *N = &p.nodes[q];
-            int vc;
-            if (N->kind == K_LEAF)
-                vc = 1;
-            else if (N->kind == K_SMALL)
-                vc = 1 + N->inner;
-            else if (N->child >= 0 && N->child + 1 < p.maxNodes)
-                vc = p.nodes[N->child].vc + p.nodes[N->child + 1].vc;
-            else {
+        int lo, hi;
+        set_level_range(p, I, i, K, r, lo, hi);
+        for (int q = lo + threadIdx.x; q < hi; q += EMIT_NT) {
+            TNode *N = &p.tnodes[q];
+            const int c = N->child;
+            if (c < 0) continue;
+            if (c + 1 < nN) {
+                N->val = __ldcg(&p.tnodes[c].val) + __ldcg(&p.tnodes[c + 1].val);
+            } else {
                 set_err(p.ctl, E_INTERNAL);
-                vc = 0;
+                N->val = 0;
             }
-            N->vc = vc;
         }
+        __threadfence_block();
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        long long o = 0;
+        int o = 0;
         for (int k = 0; k < K; k++) {
-            Node *N = &p.nodes[I->level0 + k];
-            N->off = o;
-            o += N->vc;
+            TNode *N = &p.tnodes[I->level0 + k];
+            const int v = __ldcg(&N->val);
+            N->val = o;
+            o += v;
         }
-        p.outCounts[i] = (int)o;
+        p.outCounts[i] = o;
     }
+    __threadfence_block();
     __syncthreads();
     for (int r = 0; r < nL; r++) {
-        for (int q = lo_s[r] + threadIdx.x; q < hi_s[r]; q += EMIT_NT) {
-            Node *N = &p.nodes[q];
-            if (N->kind == K_BIG) {
-                if (N->child < 0 || N->child + 1 >= p.maxNodes) continue;
-                Node *A = &p.nodes[N->child];
-                Node *B = &p.nodes[N->child + 1];
-                A->off = N->off;
-                B->off = N->off + A->vc;
-            } else if (N->off >= 0 && N->off < I->n) {
-                p.outIdx[off + N->off] = N->h.idx;
+        int lo, hi;
+        set_level_range(p, I, i, K, r, lo, hi);
+        for (int q = lo + threadIdx.x; q < hi; q += EMIT_NT) {
+            const TNode *N = &p.tnodes[q];
+            const int c = N->child, o = __ldcg(&N->val);
+            if (c >= 0) {
+                if (c + 1 >= nN) continue;
+                const int a = __ldcg(&p.tnodes[c].val);
+                p.tnodes[c].val = o;
+                p.tnodes[c + 1].val = o + a;
+            } else if (o >= 0 && o < n) {
+                p.outIdx[off + o] = N->head;
             } else {
                 set_err(p.ctl, E_INTERNAL);
             }
         }
+        __threadfence_block();
         __syncthreads();
     }
 }
 
+// The inner vertices of every small segment after its head.
 __global__ void copy_kernel(Params p) {
     if (p.ctl->err != 0u) return;
     const int nSN = p.ctl->nSmall;
     for (int w = blockIdx.x; w < nSN; w += gridDim.x) {
-        const Node *N = &p.nodes[p.smallQ[w]];
-        const int inner = N->inner;
-        if (N->off < 0 || N->off + 1 + inner > p.inst[N->inst].n || inner > N->count) {
+        const SmallRec *R = &p.small[w];
+        const int inner = R->cIdx, count = R->count;
+        const Inst *I = &p.inst[R->inst];
+        const int o = p.tnodes[R->tree].val;
+        if (o < 0 || o + 1 + (long long)inner > I->n || inner > count || inner < 0) {
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             continue;
         }
-        int *dst = p.outIdx + p.inst[N->inst].off + N->off + 1;
-        const int *src = p.vscratch + N->pstart;
+        int *dst = p.outIdx + I->off + o + 1;
+        const int *src = p.vscratch + R->pstart;
         for (int k = threadIdx.x; k < inner; k += blockDim.x) dst[k] = src[k];
     }
 }

@@ -30,8 +30,8 @@ constexpr int TILE = NT * IPT;     // points per tile
 constexpr int TILE_MIN = 128 * IPT;  // smallest tile of the compiled variants (sizes the plans)
 constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
 constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
-constexpr int MAX_LEVELS = 48;     // grid-wide rounds (deeper recursions report QH_ERR_CAPACITY)
-constexpr int MAX_GEN = 64;        // generations tracked in the statistics
+constexpr int MAX_GEN = 512;       // generations tracked in the statistics (deeper ones add to the last)
+constexpr int MAX_STAMPS = 64;     // grid-phase timestamps kept in the statistics
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // polls (with back-off) before a wait gives up
 
 // device-side error bits (ctl->err)
@@ -64,19 +64,38 @@ struct Inst {
     Cand chC[4];       // farthest point of each initial segment
 };
 
-// A segment of the grid-wide rounds: its chord h->e, its points
-// [pstart, pstart + count) of live buffer `buf`, and its farthest point c.
+// A segment of the grid-wide rounds while it is active: its chord h->e, its
+// points [pstart, pstart + count) of live buffer `buf`, and its farthest point
+// c.  Records live in a ring of two levels (the level a round reads and the
+// level it creates); the segment tree itself is kept in TNode.
 struct Node {
     Cand h, e, c;
     int count, kind;
     long long pstart;
-    int buf, inst, level, child;  // child: index of the first of its two children (K_BIG)
+    int buf, inst, level, tree;   // tree: the segment's TNode
     int chCount[2];               // points of the two children: output cursors during the round (atomic)
     Cand chC[2];                  // farthest points of the two children
-    int inner, vc;                // inner vertices (K_SMALL), vertices of the subtree
-    long long off;                // output offset of the subtree within its set
     unsigned tdone;               // tiles of the round that finished with this segment (atomic)
     int pad2[3];
+};
+
+// A node of the segment tree of the grid-wide rounds (16 bytes).  Nodes are
+// stored level by level, every level grouped by set in set order.  child: the
+// first of the two children of a split segment, -1 for a leaf (a segment that
+// ended empty or went to the block finisher).  val: vertices of the subtree,
+// then (output pass) the subtree's output offset within its set.
+// Every node's head is a distinct hull vertex of its set and a split segment
+// has two children, so a set of n points has at most 2n nodes.
+struct TNode {
+    int child, head, val, inst;
+};
+
+// A segment handed to the block finisher.  Coordinates of h and e are read
+// from the input through their indices (local to the set).  cIdx is replaced
+// by the number of inner vertices once the segment is finished.
+struct SmallRec {
+    int hIdx, eIdx, cIdx, count;
+    int pstart, level, inst, tree;
 };
 
 // Extreme points of a tile: lexicographic min/max of (x, y) and of (y, x).
@@ -96,8 +115,7 @@ struct Ctl {
     int cur;             // bigList buffer of the current round
     long long L;         // points of the current round
     long long tiles;     // tiles of the current round
-    int nLevels, nNodes;
-    int levelBase[MAX_LEVELS + 2];
+    int nLevels, nNodes; // levels and TNodes of the segment tree
     int nSmall;          // small-segment queue length
     unsigned finTicket;
     int rounds;          // grid-wide rounds run after the initial split
@@ -108,7 +126,7 @@ struct Ctl {
     int gens;            // generations run (max over sets)
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;
-    unsigned long long tphase[MAX_LEVELS + 4];  // %globaltimer at the kernel start and after each grid barrier
+    unsigned long long tphase[MAX_STAMPS];  // %globaltimer at the kernel start and after each grid barrier
     unsigned long long prof[48];                // section cycle counters (profiling builds only)
 };
 
@@ -130,12 +148,18 @@ struct Params {
     Inst *inst;
     int *bigInst, *smallInst;
     long long *bigTilePrefix;  // exclusive prefix of tiles over big sets (nBig + 1)
-    Node *nodes;
-    int maxNodes;
+    Node *nodes;               // ring of two levels of active segments, slotCap each
+    int slotCap;
+    TNode *tnodes;             // segment tree
+    int maxTNodes;
+    int *levelBase;            // first TNode of every level (maxLevels + 1 entries)
+    int maxLevels;
+    SmallRec *small;           // small-segment queue
+    int maxSmall;
+    unsigned spinLimit;        // polls of a grid-barrier wait before it gives up
     int *bigList[2];
     long long *vstart[2];      // exclusive prefix of big-segment sizes (S + 1)
     int maxBig;
-    int *smallQ;
     Ctl *ctl;
     int cut;                   // small-segment cutover
 };
@@ -220,14 +244,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Phase timestamp, written by CTA 0 after a grid barrier.
 __device__ __forceinline__ void stamp(Ctl *ctl, int k) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && k < MAX_LEVELS + 4) ctl->tphase[k] = global_ns();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && k < MAX_STAMPS) ctl->tphase[k] = global_ns();
 }
 
 // Grid-wide barrier for a cooperative launch.  Every CTA increments `bar`
 // once per barrier; phase counts barriers passed by this CTA.  The wait is
 // bounded: on timeout (or when another CTA reported an error) the error bit is
 // set and false is returned so the kernel can leave.
-__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase) {
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase, unsigned limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -242,7 +266,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase) {
                 ok = 0;
                 break;
             }
-            if (++it > SPIN_LIMIT) {
+            if (++it > limit) {
                 set_err(ctl, E_TIMEOUT);
                 ok = 0;
                 break;
@@ -262,7 +286,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase) {
 // other CTAs wait for that release and return 0.  -1: an error was reported
 // or the wait timed out (the error bit is set).  One atomic round trip
 // instead of a separate "last CTA" count followed by a barrier.
-__device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase) {
+__device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase, unsigned limit) {
     __shared__ int s_role;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -279,7 +303,7 @@ __device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase) {
                     role = -1;
                     break;
                 }
-                if (++it > SPIN_LIMIT) {
+                if (++it > limit) {
                     set_err(ctl, E_TIMEOUT);
                     role = -1;
                     break;
@@ -366,12 +390,10 @@ __device__ __forceinline__ unsigned pkey_up(double d) { return fkey(__double2flo
 namespace v256 {
 cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
 int rounds_max_ctas_per_sm(int prec);
-int prof_cta_copy(void *host, int n);
 }  // namespace v256
 namespace v128 {
 cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
 int rounds_max_ctas_per_sm(int prec);
-int prof_cta_copy(void *host, int n);
 }  // namespace v128
 struct RoundsVariant {
     int threads, tile;

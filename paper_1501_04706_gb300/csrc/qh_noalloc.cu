@@ -7,7 +7,7 @@
 // components.  This entry point takes its scratch from one file-scope
 // __device__ array of fixed size instead of a plan, so it allocates nothing
 // (the array is part of the library's device image: every GPU that loads the
-// library holds it, about 16 MB, until the process exits).
+// library holds it, about 31 MB, until the process exits).
 //
 // The work itself is the library's regular kernel sequence (grid-wide rounds in
 // the 256-thread variant,
@@ -29,7 +29,12 @@ constexpr long long NA_N = QH_NOALLOC_MAX_POINTS;
 constexpr long long NA_SETS = 1;
 constexpr long long NA_TILES = NA_N / TILE + NA_SETS + 16;
 constexpr long long NA_BIG = NA_N / TILE + 16;
-constexpr long long NA_NODES = 4 * NA_SETS + 16ll * 2 * NA_BIG + 4096;
+// Ring slot of active segments, and the segment tree, small-segment queue and
+// level table sized for any input of NA_N points (as in a plan).
+constexpr long long NA_SLOT = (4 * NA_SETS > 2 * NA_BIG ? 4 * NA_SETS : 2 * NA_BIG) + 16;
+constexpr long long NA_TNODES = 2 * NA_N + 64;
+constexpr long long NA_LEVELS = NA_N + 2;
+constexpr long long NA_SMALL = NA_N + 64;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -46,12 +51,14 @@ constexpr size_t NA_SIZES[] = {
     sizeof(int) * (NA_SETS + 1),     // bigInst
     sizeof(int) * (NA_SETS + 1),     // smallInst
     sizeof(long long) * (NA_SETS + 2),  // bigTilePrefix
-    sizeof(Node) * NA_NODES,         // nodes
+    sizeof(Node) * 2 * NA_SLOT,      // nodes (ring of two levels)
     sizeof(int) * (NA_BIG + 1),      // bigList[0]
     sizeof(int) * (NA_BIG + 1),      // bigList[1]
     sizeof(long long) * (NA_BIG + 2),   // vstart[0]
     sizeof(long long) * (NA_BIG + 2),   // vstart[1]
-    sizeof(int) * NA_NODES,          // smallQ
+    sizeof(TNode) * NA_TNODES,       // tnodes
+    sizeof(int) * (NA_LEVELS + 2),   // levelBase
+    sizeof(SmallRec) * NA_SMALL,     // small
     sizeof(Ctl),                     // ctl
 };
 constexpr int NA_NBUF = sizeof(NA_SIZES) / sizeof(NA_SIZES[0]);
@@ -123,14 +130,20 @@ Params na_params(const DeviceScratch &d, const float *points, long long n, int *
     p.smallInst = reinterpret_cast<int *>(b[9]);
     p.bigTilePrefix = reinterpret_cast<long long *>(b[10]);
     p.nodes = reinterpret_cast<Node *>(b[11]);
-    p.maxNodes = (int)NA_NODES;
+    p.slotCap = (int)NA_SLOT;
     p.bigList[0] = reinterpret_cast<int *>(b[12]);
     p.bigList[1] = reinterpret_cast<int *>(b[13]);
     p.vstart[0] = reinterpret_cast<long long *>(b[14]);
     p.vstart[1] = reinterpret_cast<long long *>(b[15]);
     p.maxBig = (int)NA_BIG;
-    p.smallQ = reinterpret_cast<int *>(b[16]);
-    p.ctl = reinterpret_cast<Ctl *>(b[17]);
+    p.tnodes = reinterpret_cast<TNode *>(b[16]);
+    p.maxTNodes = (int)NA_TNODES;
+    p.levelBase = reinterpret_cast<int *>(b[17]);
+    p.maxLevels = (int)NA_LEVELS;
+    p.small = reinterpret_cast<SmallRec *>(b[18]);
+    p.maxSmall = (int)NA_SMALL;
+    p.ctl = reinterpret_cast<Ctl *>(b[19]);
+    p.spinLimit = SPIN_LIMIT;
     p.cut = FIN_MAX;
     return p;
 }

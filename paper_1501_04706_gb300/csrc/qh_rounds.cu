@@ -1796,33 +1796,50 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
 }
 
 // --------------------------------------------------------------------------
-// level construction (last CTA of a round)
+// level construction (leader of the grid barrier that ends a round)
 // --------------------------------------------------------------------------
-// List the big nodes of [first, first + count) for the next round (exclusive
-// prefix of their sizes), queue the small ones for the block finisher.
+// Segment records of level r live in ring slot r & 1 (the level a round reads
+// and the level it creates); the segment tree (TNode) keeps every level, so the
+// depth of the recursion is bounded by the tables' sizes only: a set of n
+// points has at most 2n tree nodes, at most n small segments and fewer than n
+// levels (a split segment loses at least its farthest point).
+
+__device__ __forceinline__ int node_kind(int count, int cut) {
+    return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
+}
+
+// List the big segments of ring entries [first, first + count) for the next
+// round (exclusive prefix of their sizes) and queue the small ones for the
+// block finisher.
 template <typename P>
 __device__ void build_biglist(const Params &p, int first, int count, int dstBuf) {
     RoundSmem<P> &sm = round_smem<P>();
     long long *scr = sm.scanTmp;
     const int per = (count + NT - 1) / NT;
     const int b = min(count, threadIdx.x * per), e = min(count, b + per);
-    long long nb = 0, np = 0;
+    long long nb = 0, np = 0, ns = 0;
     for (int k = b; k < e; k++) {
         const Node *N = &p.nodes[first + k];
-        if (__ldcg(&N->kind) == K_BIG) {
+        const int kind = __ldcg(&N->kind);
+        if (kind == K_BIG) {
             nb++;
             np += __ldcg(&N->count);
+        } else if (kind == K_SMALL) {
+            ns++;
         }
     }
-    long long totB, totP;
+    long long totB, totP, totS;
     long long xb = block_excl_scan<long long, NT>(nb, scr, totB);
     long long xp = block_excl_scan<long long, NT>(np, scr, totP);
-    if (totB > p.maxBig) {
+    long long xs = block_excl_scan<long long, NT>(ns, scr, totS);
+    const long long s0 = __ldcg(&p.ctl->nSmall);
+    if (totB > p.maxBig || s0 + totS > p.maxSmall) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return;
     }
     int *bl = p.bigList[dstBuf];
     long long *vs = p.vstart[dstBuf];
+    xs += s0;
     for (int k = b; k < e; k++) {
         const int q = first + k;
         const Node *N = &p.nodes[q];
@@ -1833,8 +1850,18 @@ __device__ void build_biglist(const Params &p, int first, int count, int dstBuf)
             xb++;
             xp += __ldcg(&N->count);
         } else if (kind == K_SMALL) {
-            int j = atomicAdd(&p.ctl->nSmall, 1);
-            __stcg(&p.smallQ[j], q);
+            SmallRec r;
+            r.hIdx = __ldcg(&N->h.idx);
+            r.eIdx = __ldcg(&N->e.idx);
+            r.cIdx = __ldcg(&N->c.idx);
+            r.count = __ldcg(&N->count);
+            r.pstart = (int)__ldcg(&N->pstart);
+            r.level = __ldcg(&N->level);
+            r.inst = __ldcg(&N->inst);
+            r.tree = __ldcg(&N->tree);
+            SmallRec *d = &p.small[xs++];
+            __stcg(reinterpret_cast<int4 *>(d), make_int4(r.hIdx, r.eIdx, r.cIdx, r.count));
+            __stcg(reinterpret_cast<int4 *>(d) + 1, make_int4(r.pstart, r.level, r.inst, r.tree));
         }
     }
     __syncthreads();
@@ -1844,13 +1871,16 @@ __device__ void build_biglist(const Params &p, int first, int count, int dstBuf)
         p.ctl->L = totP;
         p.ctl->tiles = (totP + TILE - 1) / TILE;
         p.ctl->cur = dstBuf;
+        p.ctl->nSmall = (int)(s0 + totS);
     }
     __threadfence();
     __syncthreads();
 }
 
-__device__ __forceinline__ int node_kind(int count, int cut) {
-    return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
+// A tree node: leaves start with one vertex (their head; a small segment adds
+// its inner vertices when it is finished).
+__device__ __forceinline__ void put_tnode(const Params &p, int t, int head, int inst) {
+    __stcg(reinterpret_cast<int4 *>(&p.tnodes[t]), make_int4(-1, head, 1, inst));
 }
 
 template <typename P> __device__ __noinline__ void build_level0(const Params &p) {
@@ -1867,19 +1897,20 @@ template <typename P> __device__ __noinline__ void build_level0(const Params &p)
         }
         long long tot;
         long long x = block_excl_scan<long long, NT>(K, scr, tot);
-        if (carry + tot > p.maxNodes) {
+        if (carry + tot > p.slotCap || carry + tot > p.maxTNodes) {
             if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
             return;
         }
         if (j < nBig) {
             Inst *I = &p.inst[i];
-            const int q0 = (int)(carry + x);
+            const int q0 = (int)(carry + x);  // ring slot 0 and tree nodes both start at 0
             __stcg(&I->level0, q0);
             const long long off = __ldcg(&I->off), n = __ldcg(&I->n);
             for (int k = 0; k < K; k++) {
                 Node *N = &p.nodes[q0 + k];
                 const int cnt = __ldcg(&I->chCount[k]);
-                stcg_cand(&N->h, ldcg_cand(&I->poly[k]));
+                const Cand h = ldcg_cand(&I->poly[k]);
+                stcg_cand(&N->h, h);
                 stcg_cand(&N->e, ldcg_cand(&I->poly[(k + 1) % K]));
                 stcg_cand(&N->c, ldcg_cand(&I->chC[k]));
                 __stcg(&N->count, cnt);
@@ -1888,11 +1919,11 @@ template <typename P> __device__ __noinline__ void build_level0(const Params &p)
                 __stcg(&N->buf, 0);
                 __stcg(&N->inst, i);
                 __stcg(&N->level, 0);
-                __stcg(&N->child, -1);
-                __stcg(&N->inner, 0);
+                __stcg(&N->tree, q0 + k);
                 __stcg(&N->chCount[0], 0);
                 __stcg(&N->chCount[1], 0);
                 __stcg(&N->tdone, 0u);
+                put_tnode(p, q0 + k, h.idx, i);
             }
         }
         carry += tot;
@@ -1902,21 +1933,23 @@ template <typename P> __device__ __noinline__ void build_level0(const Params &p)
     if (threadIdx.x == 0) {
         p.ctl->nNodes = (int)carry;
         p.ctl->nLevels = 1;
-        p.ctl->levelBase[0] = 0;
-        p.ctl->levelBase[1] = (int)carry;
+        p.levelBase[0] = 0;
+        p.levelBase[1] = (int)carry;
     }
     build_biglist<P>(p, 0, (int)carry, 0);
 }
 
+// Level r from the big segments of level r - 1 (ring slot (r - 1) & 1): each
+// (h, e) with farthest point c becomes (h, c) and (c, e) in slot r & 1.
 template <typename P> __device__ __noinline__ void build_level(const Params &p, int r) {
-    RoundSmem<P> &sm = round_smem<P>();
     const int S = __ldcg(&p.ctl->S);
     const int cur = __ldcg(&p.ctl->cur);
     const int base = __ldcg(&p.ctl->nNodes);
-    if (base + 2ll * S > p.maxNodes || r + 1 > MAX_LEVELS) {
+    if ((long long)base + 2ll * S > p.maxTNodes || 2ll * S > p.slotCap || r + 1 > p.maxLevels) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return;
     }
+    const int slot = (r & 1) * p.slotCap;
     const int *bl = p.bigList[cur];
     for (int j = threadIdx.x; j < S; j += NT) {
         const int q = __ldcg(&bl[j]);
@@ -1924,9 +1957,9 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
         const Cand h = ldcg_cand(&Q->h), e = ldcg_cand(&Q->e), c = ldcg_cand(&Q->c);
         const long long ps = __ldcg(&Q->pstart);
         const int cnt = __ldcg(&Q->count), buf = __ldcg(&Q->buf), inst = __ldcg(&Q->inst);
-        __stcg(&Q->child, base + 2 * j);
+        __stcg(&p.tnodes[__ldcg(&Q->tree)].child, base + 2 * j);
         for (int w = 0; w < 2; w++) {
-            Node *N = &p.nodes[base + 2 * j + w];
+            Node *N = &p.nodes[slot + 2 * j + w];
             const int cc = __ldcg(&Q->chCount[w]);
             stcg_cand(&N->h, w ? c : h);
             stcg_cand(&N->e, w ? e : c);
@@ -1937,11 +1970,11 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
             __stcg(&N->buf, buf ^ 1);
             __stcg(&N->inst, inst);
             __stcg(&N->level, r);
-            __stcg(&N->child, -1);
-            __stcg(&N->inner, 0);
+            __stcg(&N->tree, base + 2 * j + w);
             __stcg(&N->chCount[0], 0);
             __stcg(&N->chCount[1], 0);
             __stcg(&N->tdone, 0u);
+            put_tnode(p, base + 2 * j + w, w ? c.idx : h.idx, inst);
         }
     }
     __threadfence();
@@ -1949,10 +1982,10 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
     if (threadIdx.x == 0) {
         p.ctl->nNodes = base + 2 * S;
         p.ctl->nLevels = r + 1;
-        p.ctl->levelBase[r + 1] = base + 2 * S;
+        p.levelBase[r + 1] = base + 2 * S;
         p.ctl->rounds = r;
     }
-    build_biglist<P>(p, base, 2 * S, cur ^ 1);
+    build_biglist<P>(p, slot, 2 * S, cur ^ 1);
 }
 
 // --------------------------------------------------------------------------
@@ -1981,11 +2014,11 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         tl_reset();
 #endif
     }
-    if (!grid_sync(p.ctl, phase)) goto out;
+    if (!grid_sync(p.ctl, phase, p.spinLimit)) goto out;
     stamp(p.ctl, 1);
 
     phase_extremes<P>(p, gI, gC);
-    if (!grid_sync(p.ctl, phase)) goto out;
+    if (!grid_sync(p.ctl, phase, p.spinLimit)) goto out;
     stamp(p.ctl, 2);
 
     phase_round0<P>(p, gI, gC, exact_o, exact_c, surv);
@@ -1998,7 +2031,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     }
     surv = 0;
     {
-        const int role = grid_arrive(p.ctl, phase);
+        const int role = grid_arrive(p.ctl, phase, p.spinLimit);
         if (role < 0) goto out;
         if (role == 1) {  // the last CTA builds the first level
 #ifdef QH_PROFILE
@@ -2034,7 +2067,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->gridRead += L;
         surv = 0;
-        const int role = grid_arrive(p.ctl, phase);
+        const int role = grid_arrive(p.ctl, phase, p.spinLimit);
         if (role < 0) goto out;
         if (role == 1) {  // the last CTA builds the next level
 #ifdef QH_PROFILE
@@ -2086,16 +2119,6 @@ cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s) {
                                        sizeof(RoundSmem<float>), s);
 }
 
-#ifndef QH_PROFILE
-int prof_cta_copy(void *, int) { return -1; }
-#else
-int prof_cta_copy(void *host, int n) {
-    return cudaMemcpyFromSymbol(host, qh_prof_cta, sizeof(unsigned long long) * 8 * (size_t)min(n, 1024)) ==
-                   cudaSuccess
-               ? 0
-               : -1;
-}
-#endif
 
 int rounds_max_ctas_per_sm(int prec) {
     int b = 0;

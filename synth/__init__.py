@@ -24,12 +24,20 @@ tests):
 5. ``batched`` -- 4096 independent sets, size floor(64 * 4096^U) clamped to
    [64, 262144], each drawn uniform-square, uniform-disk or standard-Gaussian with
    equal probability; CSR int64 offsets.
+
+Stress input (not one of the five workloads):
+
+6. ``parabola`` -- points in convex position on y = x^2 with x = fl32(U^100):
+   the x-values spread over dozens of binary orders of magnitude, so every
+   QuickHull round splits a segment near the middle of its x-range and most of
+   its points stay in one child; at 1,000,000 points the recursion runs about
+   80 generations deep (a third of the points underflow to the origin).
 """
 from __future__ import annotations
 
 import numpy as np
 
-CONFIG_IDS = {"square": 1, "disk": 2, "circle": 3, "degenerate": 4, "batched": 5}
+CONFIG_IDS = {"square": 1, "disk": 2, "circle": 3, "degenerate": 4, "batched": 5, "parabola": 6}
 
 FULL_SIZES = {
     "square": 100_000,
@@ -37,6 +45,7 @@ FULL_SIZES = {
     "circle": 20_000_000,
     "degenerate": 16_000_000,
     "batched": 4096,  # number of sets
+    "parabola": 1_000_000,
 }
 
 
@@ -124,10 +133,18 @@ def batched(num_sets: int = FULL_SIZES["batched"], seed: int = 0, min_size: int 
     return pts, offsets
 
 
+def parabola(n: int = FULL_SIZES["parabola"], seed: int = 0, power: int = 100) -> np.ndarray:
+    """Deep-recursion stress: x = fl32(U^power), y = fl32(x^2) as float32[n, 2]."""
+    rng = _rng(CONFIG_IDS["parabola"], seed)
+    x = (rng.random(n) ** power).astype(np.float32)
+    y = (x.astype(np.float64) ** 2).astype(np.float32)
+    return np.stack([x, y], axis=1)
+
+
 def make(name: str, n: int | None = None, seed: int = 0):
     """Generate a workload by name; ``n`` overrides the default size (sets for ``batched``)."""
     fn = {"square": square, "disk": disk, "circle": circle, "degenerate": degenerate,
-          "batched": batched}[name]
+          "batched": batched, "parabola": parabola}[name]
     if n is None:
         return fn(seed=seed)
     return fn(n, seed=seed)
