@@ -138,15 +138,65 @@ def test_batched_matches_per_set(qh):
     plan.close()
 
 
+_FULL = {}
+
+
+def _full(name, n=None):
+    """A full-size workload and its oracle hull (the last one is kept for the next test)."""
+    key = (name, n)
+    if key not in _FULL:
+        _FULL.clear()
+        p = synth.make(name) if n is None else synth.make(name, n)
+        _FULL[key] = (p, oracle.hull2d(p))
+    return _FULL[key]
+
+
+def test_config1_as_stated(qh):
+    """Configuration 1 exactly: 100,000 points uniform in [0,1)^2 from seed 0, plain FP64 predicates
+    (and the FP32 filtered form), bit-exact against the monotone-chain oracle."""
+    p = synth.square()
+    assert p.shape == (100_000, 2)
+    want = oracle.hull2d(p)
+    for prec in (qh.PREC_F64, qh.PREC_F32):
+        for mode in (qh.MODE_QUAD, qh.MODE_CHORD):
+            plan = qh.Plan(len(p), 1, mode=mode, prec=prec)
+            assert np.array_equal(_hull(qh, plan, p), want), (mode, prec)
+            assert plan.stats()["device_status"] == 0
+            plan.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["quad", "chord"])
+@pytest.mark.parametrize("name", ["disk", "circle", "degenerate"])
+def test_full_size(qh, name, mode):
+    p, want = _full(name)
+    plan = qh.Plan(len(p), 1, mode=qh.MODE_QUAD if mode == "quad" else qh.MODE_CHORD)
+    got = _hull(qh, plan, p)
+    assert np.array_equal(got, want), (len(got), len(want))
+    plan.close()
+    if mode == "quad":
+        check_hull_invariants(p[:200_000], oracle.hull2d(p[:200_000]))
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["disk", "circle", "degenerate"])
-def test_full_size(qh, name):
-    p = synth.make(name)
+def test_full_size_plain_fp64(qh, name):
+    """Configuration 2's plain-FP64 form (and the same form on configurations 3 and 4)."""
+    p, want = _full(name)
+    plan = qh.Plan(len(p), 1, prec=qh.PREC_F64)
+    assert np.array_equal(_hull(qh, plan, p), want)
+    plan.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [2_000_000, 20_000_000])
+def test_square_sweep_sizes(qh, n):
+    """The unit-square size sweep (Table 2 shapes) at 2M and 20M points, both initial splits."""
+    p, want = _full("square", n)
     plan = qh.Plan(len(p), 1)
-    got = _hull(qh, plan, p)
-    want = oracle.hull2d(p)
-    assert np.array_equal(got, want)
-    check_hull_invariants(p[:200_000], oracle.hull2d(p[:200_000]))
+    for mode in (qh.MODE_QUAD, qh.MODE_CHORD):
+        plan.set_flags(mode, qh.PREC_F32)
+        assert np.array_equal(_hull(qh, plan, p), want), mode
     plan.close()
 
 
