@@ -106,20 +106,22 @@ qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags);
 
 /*
  * Tuning knobs.  cutover: segments with at most this many points are finished
- * by one thread block in shared memory; from the grid-wide tile size of the
- * plan's block size (so a tile never spans more than two segments) to 4096.  timing: 1
- * records CUDA events between the kernels so qh_plan_get_stats can report
- * per-phase times.  grid_ctas_per_sm: 0 = occupancy maximum.
+ * by one thread block in shared memory; from the grid-wide tile of the plan's
+ * kernel variant (32 x points per thread, so a tile never spans more than two
+ * segments) to 4096.  timing: 1 records CUDA events between the kernels so
+ * qh_plan_get_stats can report per-phase times.  grid_ctas_per_sm: 0 =
+ * occupancy maximum.
  */
 qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int32_t grid_ctas_per_sm);
 
 /*
- * Block size of the grid-wide kernel: 256 (tiles of 4096 points, 2 CTAs per SM) or 128 threads (tiles of
- * 2048 points, 4 CTAs per SM); 16 points per thread in both.  Raises the cutover to the new tile size if
- * needed and resets grid_ctas_per_sm to the occupancy maximum.  Other values: QH_ERR_INVALID_ARG.
- * (Not in the paper: its kernels are Thrust calls with library-chosen launch shapes.)
+ * Kernel variant of the grid-wide rounds: threads per block (256 or 128) and points per thread per tile (16
+ * or 8; a tile is one warp's unit of work, 32 x points per thread).  Each call keeps the other knob, raises
+ * the cutover to the new tile if needed and resets grid_ctas_per_sm to the occupancy maximum.  Other values:
+ * QH_ERR_INVALID_ARG.  (Not in the paper: its kernels are Thrust calls with library-chosen launch shapes.)
  */
 qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block);
+qh_status qh_plan_set_items_per_thread(qh_plan plan, int32_t items_per_thread);
 
 /*
  * Debug limits for tests of the device-side error paths (not in the paper).  spin_limit: polls (each
@@ -135,10 +137,10 @@ qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *
                              int32_t *cutover, int32_t *grid_ctas_per_sm);
 
 /*
- * Autotuner (not in the paper): hulls the caller's input once per candidate setting -- every block size,
- * grid CTAs per SM from the occupancy maximum down to half of it, and every cutover from the tile size to
- * 4096 in steps of 1024 -- timing `reps` runs of each with CUDA events on `stream`, and keeps the fastest
- * setting in the plan.  offsets == NULL: one set of n points (as qh_hull2d_p); otherwise a CSR batch (as
+ * Autotuner (not in the paper): hulls the caller's input once per candidate setting -- every kernel variant
+ * (block size x points per thread), grid CTAs per SM from the occupancy maximum down to half of it, and the
+ * cutovers 1024, 2048 and 4096 -- timing `reps` runs of each with CUDA events on `stream`, and keeps the
+ * fastest setting in the plan.  offsets == NULL: one set of n points (as qh_hull2d_p); otherwise a CSR batch (as
  * qh_hull2d_batched, n ignored).  Synchronizes the stream; out_idx / out_counts are overwritten by every
  * trial and end up holding the (identical) result of the last.  reps in [1, 64], else
  * QH_ERR_INVALID_ARG; a failing trial's status is returned and the previous best kept.

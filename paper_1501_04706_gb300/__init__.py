@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
     lib.qh_plan_set_tuning.argtypes = [vp, i32, i32, i32]
     lib.qh_plan_set_block.argtypes = [vp, i32]
     lib.qh_plan_set_debug.argtypes = [vp, u32, i32]
+    lib.qh_plan_set_items_per_thread.argtypes = [vp, i32]
     lib.qh_hull2d_noalloc.argtypes = [vp, i64, vp, vp, vp]
     lib.qh_plan_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32)]
@@ -85,7 +86,7 @@ def load() -> ctypes.CDLL:
     lib.qh_check_dist_host.argtypes = [vp, i64, vp]
     lib.qh_check_dist_device.argtypes = [vp, i64, vp, vp]
     for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_plan_set_block",
-              "qh_plan_set_debug", "qh_hull2d_noalloc",
+              "qh_plan_set_debug", "qh_hull2d_noalloc", "qh_plan_set_items_per_thread",
               "qh_plan_get_tuning", "qh_plan_autotune", "qh_hull2d_p",
               "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_plan_get_stats", "qh_check_orient_host",
               "qh_check_orient_device", "qh_check_dist_host", "qh_check_dist_device"):
@@ -135,8 +136,12 @@ class Plan:
                "qh_plan_set_tuning")
 
     def set_block(self, threads: int) -> None:
-        """Block size of the grid-wide kernel: 256 or 128 threads (16 points per thread)."""
+        """Block size of the grid-wide kernel: 256 or 128 threads."""
         _check(load().qh_plan_set_block(self.handle, int(threads)), "qh_plan_set_block")
+
+    def set_items_per_thread(self, ipt: int) -> None:
+        """Points per thread per tile of the grid-wide kernel: 16 or 8 (a tile is 32 x ipt points)."""
+        _check(load().qh_plan_set_items_per_thread(self.handle, int(ipt)), "qh_plan_set_items_per_thread")
 
     def set_debug(self, spin_limit: int = 0, max_tree_nodes: int = 0) -> None:
         """Debug limits for the device-side error paths (0 = default): grid-barrier polls before a

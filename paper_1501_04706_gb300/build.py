@@ -19,9 +19,12 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu", "qh_noalloc.cu"]
 # Translation units: (source, object name, flags).  The grid-wide kernel is compiled once per variant
-# (threads per CTA, CTAs per SM), each in its own namespace; the plan picks one at run time.
-UNITS = [("qh_rounds.cu", "qh_rounds_v256", ["-DQH_NT=256", "-DQH_MINB=2", "-DQH_VARIANT_NS=v256"]),
-         ("qh_rounds.cu", "qh_rounds_v128", ["-DQH_NT=128", "-DQH_MINB=4", "-DQH_VARIANT_NS=v128"]),
+# (threads per CTA, points per thread, CTAs per SM it is built for), each in its own namespace; the plan
+# picks one at run time.
+UNITS = [("qh_rounds.cu", "qh_rounds_v256", ["-DQH_NT=256", "-DQH_IPT=16", "-DQH_MINB=2", "-DQH_VARIANT_NS=v256"]),
+         ("qh_rounds.cu", "qh_rounds_v256i8", ["-DQH_NT=256", "-DQH_IPT=8", "-DQH_MINB=3", "-DQH_VARIANT_NS=v256i8"]),
+         ("qh_rounds.cu", "qh_rounds_v128", ["-DQH_NT=128", "-DQH_IPT=16", "-DQH_MINB=4", "-DQH_VARIANT_NS=v128"]),
+         ("qh_rounds.cu", "qh_rounds_v128i8", ["-DQH_NT=128", "-DQH_IPT=8", "-DQH_MINB=6", "-DQH_VARIANT_NS=v128i8"]),
          ("qh_finish.cu", "qh_finish", []),
          ("qh_api.cu", "qh_api", []),
          ("qh_noalloc.cu", "qh_noalloc", [])]

@@ -17,7 +17,7 @@ struct qh_plan_s {
     long long ncap = 0;
     int maxSets = 0;
     unsigned flags = 0;
-    int cut = 16 * 256;  // small-segment cutover (>= the tile of the variant)
+    int cut = FIN_MAX;   // small-segment cutover (>= the tile of the variant)
     int variant = 0;     // grid-wide kernel variant (rounds_variant)
     int timing = 0;
     int ctasPerSm = 0;
@@ -312,16 +312,27 @@ qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int3
     return QH_OK;
 }
 
-qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block) {
-    if (!plan) return QH_ERR_INVALID_ARG;
+namespace {
+qh_status select_variant(qh_plan plan, int threads, int ipt) {
     for (int v = 0; v < NUM_ROUNDS_VARIANTS; v++)
-        if (rounds_variant(v).threads == threads_per_block) {
+        if (rounds_variant(v).threads == threads && rounds_variant(v).ipt == ipt) {
             plan->variant = v;
             if (plan->cut < rounds_variant(v).tile) plan->cut = rounds_variant(v).tile;
             plan->ctasPerSm = 0;
             return QH_OK;
         }
     return QH_ERR_INVALID_ARG;
+}
+}  // namespace
+
+qh_status qh_plan_set_block(qh_plan plan, int32_t threads_per_block) {
+    if (!plan) return QH_ERR_INVALID_ARG;
+    return select_variant(plan, threads_per_block, rounds_variant(plan->variant).ipt);
+}
+
+qh_status qh_plan_set_items_per_thread(qh_plan plan, int32_t items_per_thread) {
+    if (!plan) return QH_ERR_INVALID_ARG;
+    return select_variant(plan, rounds_variant(plan->variant).threads, items_per_thread);
 }
 
 qh_status qh_plan_set_debug(qh_plan plan, uint32_t spin_limit, int32_t max_tree_nodes) {
@@ -336,7 +347,7 @@ qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *
     if (!plan) return QH_ERR_INVALID_ARG;
     const RoundsVariant &V = rounds_variant(plan->variant);
     if (threads_per_block) *threads_per_block = V.threads;
-    if (items_per_thread) *items_per_thread = V.tile / V.threads;
+    if (items_per_thread) *items_per_thread = V.ipt;
     if (cutover) *cutover = plan->cut;
     if (grid_ctas_per_sm) {
         const int mx = V.max_ctas_per_sm((plan->flags & QH_PREC_F64) ? 1 : 0);

@@ -22,12 +22,15 @@ namespace qh {
 #ifndef QH_MINB
 #define QH_MINB 2
 #endif
+#ifndef QH_IPT
+#define QH_IPT 16
+#endif
 constexpr int NT = QH_NT;          // threads per CTA of the grid-wide kernel
 constexpr int MINB = QH_MINB;      // CTAs per SM the grid-wide kernel is built for
 constexpr int NWARP = NT / 32;
-constexpr int IPT = 16;            // points per thread per tile (warp-striped rows)
+constexpr int IPT = QH_IPT;        // points per thread per tile (warp-striped rows): 16 or 8
 constexpr int TILE = NT * IPT;     // points per tile
-constexpr int TILE_MIN = 128 * IPT;  // smallest tile of the compiled variants (sizes the plans)
+constexpr int TILE_MIN = 128 * 8;  // smallest tile of the compiled variants (sizes the plans)
 constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
 constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
 constexpr int MAX_GEN = 512;       // generations tracked in the statistics (deeper ones add to the last)
@@ -104,10 +107,15 @@ struct Ext {
     int nonfinite, pad[3];
 };
 
-struct Ctl {
+// The words that waiting CTAs poll (err, bar, gen) sit on their own 128-byte
+// lines, so the polls do not queue in front of the ordinary reads of the block.
+struct alignas(128) Ctl {
     unsigned err;
+    unsigned padErr[31];
     unsigned bar;        // grid barrier arrivals (monotonic within a launch)
+    unsigned padBar[31];
     unsigned gen;        // barriers released by their leader (monotonic within a launch)
+    unsigned padGen[31];
     int nBig, nSmallInst;
     int pad0;
     long long bigTiles;  // tiles over all big sets
@@ -127,7 +135,6 @@ struct Ctl {
     long long live[MAX_GEN];
     unsigned long long exactOrient, exactCmp;
     unsigned long long tphase[MAX_STAMPS];  // %globaltimer at the kernel start and after each grid barrier
-    unsigned long long prof[48];                // section cycle counters (profiling builds only)
 };
 
 struct Params {
@@ -214,34 +221,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Section cycle counters of thread 0, compiled in with -DQH_PROFILE.
-#ifdef QH_PROFILE
-#define QH_PROF_DECL unsigned long long qh_prof_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}; long long qh_prof_t = clock64()
-#define QH_PROF(k)                                         \
-    do {                                                   \
-        if (threadIdx.x == 0) {                            \
-            const long long qh_now = clock64();            \
-            qh_prof_acc[k] += (unsigned long long)(qh_now - qh_prof_t); \
-            qh_prof_t = qh_now;                            \
-        }                                                  \
-    } while (0)
-#define QH_PROF_FLUSH(ctl)                                                    \
-    do {                                                                      \
-        if (threadIdx.x == 0)                                                 \
-            for (int qh_k = 0; qh_k < 8; qh_k++) atomicAdd(&(ctl)->prof[qh_k], qh_prof_acc[qh_k]); \
-    } while (0)
-#define QH_PROF_FLUSH_AT(ctl, base)                                           \
-    do {                                                                      \
-        if (threadIdx.x == 0)                                                 \
-            for (int qh_k = 0; qh_k < 8; qh_k++) atomicAdd(&(ctl)->prof[(base) + qh_k], qh_prof_acc[qh_k]); \
-    } while (0)
-#else
-#define QH_PROF_DECL
-#define QH_PROF(k)
-#define QH_PROF_FLUSH(ctl)
-#define QH_PROF_FLUSH_AT(ctl, base)
-#endif
-
 // Phase timestamp, written by CTA 0 after a grid barrier.
 __device__ __forceinline__ void stamp(Ctl *ctl, int k) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && k < MAX_STAMPS) ctl->tphase[k] = global_ns();
@@ -259,10 +238,10 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase, unsigned li
         const unsigned target = phase * gridDim.x;
         __threadfence();
         atomicAdd(&ctl->bar, 1u);
-        unsigned it = 0;
+        unsigned it = 0, ns = 32;
         int ok = 1;
         while (ld_acquire(&ctl->bar) < target) {
-            if (ld_volatile(&ctl->err) != 0u) {
+            if ((it & 7u) == 0u && ld_volatile(&ctl->err) != 0u) {
                 ok = 0;
                 break;
             }
@@ -271,7 +250,8 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase, unsigned li
                 ok = 0;
                 break;
             }
-            __nanosleep(100);
+            __nanosleep(ns);  // back-off: 32 ns doubling to 256 ns
+            ns = ns < 256u ? 2u * ns : ns;
         }
         __threadfence();
         if (ld_volatile(&ctl->err) != 0u) ok = 0;
@@ -297,9 +277,9 @@ __device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase, unsigned l
         if (d == phase * gridDim.x - 1u) {
             role = 1;
         } else {
-            unsigned it = 0;
+            unsigned it = 0, ns = 32;
             while (ld_acquire(&ctl->gen) < phase) {
-                if (ld_volatile(&ctl->err) != 0u) {
+                if ((it & 7u) == 0u && ld_volatile(&ctl->err) != 0u) {
                     role = -1;
                     break;
                 }
@@ -308,7 +288,8 @@ __device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase, unsigned l
                     role = -1;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(ns);
+                ns = ns < 256u ? 2u * ns : ns;
             }
         }
         __threadfence();
@@ -385,26 +366,30 @@ __device__ __forceinline__ unsigned pkey_up(float f) { return fkey(f); }
 __device__ __forceinline__ unsigned pkey_up(double d) { return fkey(__double2float_ru(d)); }
 
 // Host launchers (defined in the .cu files).
-// Grid-wide kernel variants: 256 threads x 16 points per tile (2 CTAs per SM)
-// and 128 threads x 16 points per tile (4 CTAs per SM).
-namespace v256 {
-cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
-int rounds_max_ctas_per_sm(int prec);
-}  // namespace v256
-namespace v128 {
-cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s);
-int rounds_max_ctas_per_sm(int prec);
-}  // namespace v128
+// Grid-wide kernel variants (threads per CTA x points per thread), each
+// compiled in its own namespace.
+#define QH_DECLARE_VARIANT(ns)                                                      \
+    namespace ns {                                                                  \
+    cudaError_t launch_rounds(const Params &p, int prec, int grid, cudaStream_t s); \
+    int rounds_max_ctas_per_sm(int prec);                                           \
+    }
+QH_DECLARE_VARIANT(v256)
+QH_DECLARE_VARIANT(v256i8)
+QH_DECLARE_VARIANT(v128)
+QH_DECLARE_VARIANT(v128i8)
+#undef QH_DECLARE_VARIANT
 struct RoundsVariant {
-    int threads, tile;
+    int threads, ipt, tile;
     cudaError_t (*launch)(const Params &, int, int, cudaStream_t);
     int (*max_ctas_per_sm)(int);
 };
-constexpr int NUM_ROUNDS_VARIANTS = 2;
+constexpr int NUM_ROUNDS_VARIANTS = 4;
 inline const RoundsVariant &rounds_variant(int v) {
     static const RoundsVariant table[NUM_ROUNDS_VARIANTS] = {
-        {256, 256 * IPT, &v256::launch_rounds, &v256::rounds_max_ctas_per_sm},
-        {128, 128 * IPT, &v128::launch_rounds, &v128::rounds_max_ctas_per_sm}};
+        {256, 16, 256 * 16, &v256::launch_rounds, &v256::rounds_max_ctas_per_sm},
+        {256, 8, 256 * 8, &v256i8::launch_rounds, &v256i8::rounds_max_ctas_per_sm},
+        {128, 16, 128 * 16, &v128::launch_rounds, &v128::rounds_max_ctas_per_sm},
+        {128, 8, 128 * 8, &v128i8::launch_rounds, &v128i8::rounds_max_ctas_per_sm}};
     return table[v];
 }
 cudaError_t launch_finish(const Params &p, int prec, int grid, cudaStream_t s);

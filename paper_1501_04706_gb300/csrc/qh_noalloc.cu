@@ -27,8 +27,8 @@ namespace {
 
 constexpr long long NA_N = QH_NOALLOC_MAX_POINTS;
 constexpr long long NA_SETS = 1;
-constexpr long long NA_TILES = NA_N / TILE + NA_SETS + 16;
-constexpr long long NA_BIG = NA_N / TILE + 16;
+constexpr long long NA_TILES = NA_N / TILE_MIN + NA_SETS + 16;
+constexpr long long NA_BIG = NA_N / TILE_MIN + 16;
 // Ring slot of active segments, and the segment tree, small-segment queue and
 // level table sized for any input of NA_N points (as in a plan).
 constexpr long long NA_SLOT = (4 * NA_SETS > 2 * NA_BIG ? 4 * NA_SETS : 2 * NA_BIG) + 16;
@@ -93,7 +93,7 @@ qh_status na_setup(int dev, DeviceScratch &d) {
     if (e != cudaSuccess || ptr == nullptr) return QH_ERR_CUDA;
     e = cudaDeviceGetAttribute(&d.numSMs, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return QH_ERR_CUDA;
-    d.ctasPerSm = v256::rounds_max_ctas_per_sm(0);
+    d.ctasPerSm = rounds_variant(0).max_ctas_per_sm(0);
     if (d.ctasPerSm < 1) return QH_ERR_CUDA;
     d.base = static_cast<unsigned char *>(ptr);
     d.ready = true;
@@ -172,7 +172,7 @@ extern "C" qh_status qh_hull2d_noalloc(const float *points, int64_t n, int32_t *
     // (counters, barrier, statistics, error bits); every other buffer is
     // initialised by the kernels before it is read
     cudaError_t e = cudaMemsetAsync(p.ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = v256::launch_rounds(p, 0, d.numSMs * d.ctasPerSm, s);
+    if (e == cudaSuccess) e = rounds_variant(0).launch(p, 0, d.numSMs * d.ctasPerSm, s);
     if (e == cudaSuccess) e = launch_finish(p, 0, d.numSMs, s);
     if (e == cudaSuccess) e = launch_emit(p, s);
     if (e == cudaSuccess) e = launch_copy(p, d.numSMs * 4, s);

@@ -188,6 +188,29 @@ QH_HD float rfma(float a, float b, float c) {
 #endif
 }
 
+QH_HD double rfma(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+    return __fma_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+// a * b rounded toward +inf.
+QH_HD float mul_up(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_ru(a, b);
+#else
+    return std::nextafter(a * b, INFINITY);
+#endif
+}
+QH_HD double mul_up(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_ru(a, b);
+#else
+    return std::nextafter(a * b, INFINITY);
+#endif
+}
+
 template <typename T> QH_HD void two_sum(T a, T b, T &s, T &e) {
     s = radd(a, b);
     const T bb = rsub(s, a);

@@ -43,21 +43,6 @@
 namespace qh {
 namespace QH_VARIANT_NS {
 
-#ifdef QH_PROFILE
-__device__ unsigned long long *qh_ctl_prof;
-__device__ __forceinline__ unsigned long long *round_ctl_prof() { return qh_ctl_prof; }
-// Per-CTA records of the initial split (profiling builds only): loop ns, SM,
-// first tile, tiles, exact orientations, exact comparisons, pass-1 and
-// pass-2 cycles.
-__device__ unsigned long long qh_prof_cta[1024][8];
-// Phase timeline (profiling builds only): rows 512 + 2 ph (latest over the
-// CTAs) and 513 + 2 ph (earliest) of qh_prof_cta hold, per event, the ns since
-// the kernel's start stamp plus 2^40.
-#define QH_TL(ph, e) tl_event(p, ph, e)
-#else
-#define QH_TL(ph, e)
-#endif
-
 constexpr int NS = 2;          // pipeline stages per CTA
 constexpr int DB = NT >= 256 ? 8 : 4;  // tile descriptors resolved per batch (one thread per tile)
 constexpr int CLS_NONE = 15;
@@ -429,20 +414,12 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
     const long long G = gridDim.x;
     const long long c0 = chunk_of(ta, T, G), c1 = chunk_of(tb, T, G);
     const long long nrec = 1 + (c1 - c0);  // record 0 at ta, then the chunks c0 + 1 .. c1
-#ifdef QH_PROFILE
-    unsigned long long mt[6];
-    mt[0] = global_ns();
-#define QH_MT(k) mt[k] = global_ns()
-#else
-#define QH_MT(k)
-#endif
     if (threadIdx.x < 4) {
         sm.mthr[threadIdx.x] = 0u;
         sm.nq[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
-    QH_MT(1);
     const bool narrow = (unsigned long long)G * (unsigned long long)(T + 1) < (1ull << 32);
     // record r: its tile (-1: none) and record slot base
     auto rec_tile = [&](long long r, int &base) -> long long {
@@ -500,7 +477,6 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         if (lane == 0 && v) atomicMax(&sm.mthr[q], v);
     }
     __syncthreads();
-    QH_MT(2);
     // pass 2: the candidates among the kept records are read again (rare)
 #pragma unroll
     for (int k = 0; k < MREC; k++) {
@@ -520,7 +496,6 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         }
     }
     __syncthreads();
-    QH_MT(3);
     if (!sm.candOver) {
         if (threadIdx.x < nslot) {
             const int q = threadIdx.x, n = sm.nq[q];
@@ -549,16 +524,9 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
         }
     }
     __syncthreads();
-    QH_MT(4);
     if (threadIdx.x < 4) sm.nq[threadIdx.x] = 0;
     if (threadIdx.x == 0) sm.candOver = 0;
     __syncthreads();
-#ifdef QH_PROFILE
-    QH_MT(5);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; k++) atomicMax(&p.ctl->prof[33 + k], mt[k + 1] - mt[k]);
-#endif
-#undef QH_MT
 }
 
 // Publish the CTA's run (record + tile count on the parent's counter); the
@@ -570,9 +538,6 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
     RoundSmem<P> &sm = round_smem<P>();
     RunAcc<P> &ra = sm.run;
     const int nslot = ra.nslot;
-#ifdef QH_PROFILE
-    const unsigned long long tf0 = global_ns();
-#endif
     if (threadIdx.x == 32) {
         for (int s = 0; s < nslot; s++) stcg_cand(&p.tbest[4 * ra.first + ra.slotBase + s], ra.best[s].c);
         __threadfence();
@@ -581,27 +546,15 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
         sm.fflag[0] = old + (unsigned)ra.tiles == (unsigned)ra.total;
     }
     __syncthreads();
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[42], global_ns() - tf0);
-#endif
     if (sm.fflag[0]) {
         __threadfence();
-#ifdef QH_PROFILE
-        const unsigned long long tm0 = global_ns();
-#endif
         merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
-#ifdef QH_PROFILE
-        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[30], global_ns() - tm0);
-#endif
         if (threadIdx.x < nslot) {
             Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
             stcg_cand(dstC, sm.fin[threadIdx.x]);
         }
     }
     __syncthreads();
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[31], global_ns() - tf0);
-#endif
     if (threadIdx.x == 0) ra.node = -1;
     __syncthreads();
 }
@@ -903,18 +856,6 @@ __device__ void pipe_refill(const Params &p, const TileSeq &q, long long k, int 
     gI++;
 }
 
-#ifdef QH_PROFILE
-__device__ __forceinline__ void tl_event(const Params &p, int ph, int e) {
-    if (threadIdx.x == 0 && ph < 32) {
-        const unsigned long long v = global_ns() - __ldcg(&p.ctl->tphase[0]) + (1ull << 40);
-        atomicMax(&qh_prof_cta[512 + 2 * ph][e], v);
-        atomicMin(&qh_prof_cta[513 + 2 * ph][e], v);
-    }
-}
-__device__ void tl_reset() {
-    for (int k = threadIdx.x; k < 64 * 8; k += NT) qh_prof_cta[512 + k / 8][k % 8] = (k / 8) & 1 ? ~0ull : 0ull;
-}
-#endif
 
 // Wait for every copy still in flight (used on the error path before leaving).
 template <typename P>
@@ -938,13 +879,6 @@ template <typename P>
 __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long segFirst, int segTiles) {
     RoundSmem<P> &sm = round_smem<P>();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#ifdef QH_PROFILE
-    unsigned long long et[6];
-    et[0] = global_ns();
-#define QH_ET(k) et[k] = global_ns()
-#else
-#define QH_ET(k)
-#endif
     e = warp_ext_reduce(e);
     __syncthreads();
     if (lane == 0) sm.wext[w] = e;
@@ -959,11 +893,7 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         __threadfence();
     }
     __syncthreads();
-    QH_ET(1);
     if (!sm.kflag) {
-#ifdef QH_PROFILE
-        if (threadIdx.x == 0) atomicMax(&p.ctl->prof[43], et[1] - et[0]);
-#endif
         return;
     }
     const Inst *I = &p.inst[i];
@@ -976,13 +906,10 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         const long long c = b * T / G;  // chunk starts inside the set hold partials too
         if (c > tile0 && c < tile0 + tiles) ext_merge(r, ld_ext(&p.text[c]));
     }
-    QH_ET(2);
     r = warp_ext_reduce(r);
-    QH_ET(3);
     __syncthreads();
     if (lane == 0) sm.wext[w] = r;
     __syncthreads();
-    QH_ET(4);
     if (threadIdx.x == 0) {
         Ext a = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(a, sm.wext[k]);
@@ -1010,13 +937,6 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         __threadfence();
     }
     __syncthreads();
-    QH_TL(0, 4);
-#ifdef QH_PROFILE
-    QH_ET(5);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; k++) atomicMax(&p.ctl->prof[43 + k], et[k + 1] - et[k]);
-#endif
-#undef QH_ET
 }
 
 // --------------------------------------------------------------------------
@@ -1072,13 +992,14 @@ __device__ __forceinline__ unsigned nibbles_equal(unsigned w, unsigned q) {
     return (t | (t >> 12)) & 0xffu;
 }
 
-// Items (bit j) of this thread whose slot is in the set fl.
+// Items (bit j < IPT) of this thread whose slot is in the set fl.  The nibbles
+// of items beyond IPT are never written (zero), so they are masked off.
 __device__ __forceinline__ unsigned items_in_slots(unsigned fl, unsigned cp0, unsigned cp1) {
     unsigned m = 0u;
 #pragma unroll
     for (int q = 0; q < 4; q++)
         if ((fl >> q) & 1u) m |= nibbles_equal(cp0, q) | (nibbles_equal(cp1, q) << 8);
-    return m;
+    return m & ((1u << IPT) - 1u);
 }
 
 __device__ __forceinline__ int item_cls(int j, unsigned cp0, unsigned cp1) {
@@ -1259,14 +1180,6 @@ template <typename P, typename Fetch>
 __device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, int nItems, Fetch &&fetch,
                                                    int &exact_c) {
     __syncthreads();
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) {
-        const int nc = sm.nq[0] + sm.nq[1] + sm.nq[2] + sm.nq[3];
-        atomicAdd(&round_ctl_prof()[38], (unsigned long long)nc);
-        atomicAdd(&round_ctl_prof()[39], 1ull);
-        atomicMax(&round_ctl_prof()[40], (unsigned long long)nc);
-    }
-#endif
     if (!sm.candOver) {
         if (threadIdx.x < nslot) {
             const int q = threadIdx.x, n = sm.nq[q];
@@ -1332,13 +1245,11 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
     q.kind = 0;
     q.S = q.cur = q.src = 0;
     q.L = 0;
-    QH_TL(0, 0);
     tile_extremes_reset(sm);
     pipe_start<P>(p, q, gI);
     Ext acc = ext_empty();
     int accInst = -1, segTiles = 0;
     long long segFirst = 0;
-    QH_PROF_DECL;
     for (long long k = 0; k < cnt; k++) {
         const int s = (int)(gC % NS);
         const unsigned par = (unsigned)((gC / NS) & 1ull);
@@ -1347,8 +1258,6 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
             pipe_drain<P>(p, gI, gC);
             return false;
         }
-        QH_PROF(0);
-        if (k == 0) QH_TL(0, 1);
         const TileRec &R = desc_of(sm, k);
         const int inst = R.inst;
         if (inst != accInst) {
@@ -1370,7 +1279,6 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
             ext_pass_a<false>(xs, dx, nItems, mnx, mxx, mny, mxy, nan);
         if (nan) acc.nonfinite = 1;
         {
-            QH_PROF(1);
             const unsigned k0 = __reduce_min_sync(0xffffffffu, fkey(mnx));
             const unsigned k1 = __reduce_max_sync(0xffffffffu, fkey(mxx));
             const unsigned k2 = __reduce_min_sync(0xffffffffu, fkey(mny));
@@ -1382,9 +1290,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
                 atomicMax(&sm.tk[3], k3);
             }
         }
-        QH_PROF(7);
         __syncthreads();
-        QH_PROF(2);
         const float t0 = fkey_inv(sm.tk[0]), t1 = fkey_inv(sm.tk[1]), t2 = fkey_inv(sm.tk[2]),
                     t3 = fkey_inv(sm.tk[3]);
         if (!(fabsf(t0) <= FLT_MAX && fabsf(t1) <= FLT_MAX && fabsf(t2) <= FLT_MAX && fabsf(t3) <= FLT_MAX))
@@ -1414,28 +1320,11 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
                 acc.top = mk_cand(v.x, v.y, id);
         }
         segTiles++;
-        QH_PROF(3);
         __syncthreads();
-        QH_PROF(4);
         tile_extremes_reset(sm);
         pipe_refill<P>(p, q, k, s, gI);
-        QH_PROF(5);
     }
-#ifdef QH_PROFILE
-    const unsigned long long tLoop = global_ns();
-#endif
-    QH_TL(0, 2);
     if (accInst >= 0) ext_flush<P>(p, acc, accInst, segFirst, segTiles);
-    QH_TL(0, 3);
-    QH_PROF(6);
-    QH_PROF_FLUSH_AT(p.ctl, 8);
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) {  // latest loop end and flush end of any CTA, ns after the phase start
-        const unsigned long long t1 = __ldcg(&p.ctl->tphase[1]);
-        atomicMax(&p.ctl->prof[24], tLoop - t1);
-        atomicMax(&p.ctl->prof[25], global_ns() - t1);
-    }
-#endif
     return true;
 }
 
@@ -1456,27 +1345,18 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
     q.kind = 1;
     q.S = q.cur = q.src = 0;
     q.L = 0;
-    QH_TL(1, 0);
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
     const unsigned lt = lanemask_lt();
     const int w = threadIdx.x >> 5;
-    QH_PROF_DECL;
-#ifdef QH_PROFILE
-    const unsigned long long gns0 = global_ns();
-    const long long clk0 = clock64();
-#endif
     for (long long kt = 0; kt < cnt; kt++) {
         const int s = (int)(gC % NS);
         const unsigned par = (unsigned)((gC / NS) & 1ull);
         gC++;
-        QH_PROF(7);
         if (!__syncthreads_and(pipe_wait(p, sm, s, par))) {
             pipe_drain<P>(p, gI, gC);
             return false;
         }
-        QH_PROF(0);
-        if (kt == 0) QH_TL(1, 1);
         tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int K = R.K, nItems = R.nItems;
@@ -1494,7 +1374,6 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             sm.vend[threadIdx.x][1] = v.y;
         }
         __syncthreads();
-        QH_PROF(0);
         // pass 1: each point against its lower- and upper-chain candidate edge
         const int iB = R.iB, dx = R.g[0].dx;
         const bool hasBot = iB == 2, hasTop = K - iB == 2;
@@ -1527,11 +1406,9 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             renote_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
         pass1_commit(sm, cp0, cp1, pc, mlo);
-        QH_PROF(2);
         Inst *W = &p.inst[R.inst];
         int *const cursors[4] = {&W->chCount[0], &W->chCount[1], &W->chCount[2], &W->chCount[3]};
         tile_reserve(sm, K, cursors);
-        QH_PROF(3);
         // pass 2: write the survivors, then offer candidates
         const long long off = R.setOff, n = R.setN;
         const int idBase = (int)(R.lt * TILE);
@@ -1570,11 +1447,6 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
                 offer_candidate(sm, c, sel4(c, thr), v.x, v.y, idBase + i);
             }
         }
-        QH_PROF(4);
-#ifdef QH_PROFILE
-        __syncthreads();  // profiling builds: separates the wait for the slowest warp
-        QH_PROF(5);
-#endif
         auto fetch = [&](int i, float &px, float &py, int &idx) {
             const float2 v = xs[i + dx];
             px = v.x;
@@ -1587,41 +1459,10 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             sm.run.tiles++;
             survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
         }
-        QH_PROF(6);
         pipe_refill<P>(p, q, kt, s, gI);
-        QH_PROF(1);
     }
     __syncthreads();
-    QH_TL(1, 2);
     if (sm.run.node >= 0) flush_run<P>(p, 1, T, exact_c);
-    QH_TL(1, 3);
-    QH_PROF_FLUSH(p.ctl);
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) {  // loop time in ns and in SM cycles (their ratio: the clock)
-        const unsigned long long dt = global_ns() - gns0;
-        atomicAdd(&p.ctl->prof[16], dt);
-        atomicAdd(&p.ctl->prof[17], (unsigned long long)(clock64() - clk0));
-        atomicMax(&p.ctl->prof[18], dt);
-        atomicMax(&p.ctl->prof[19], 1000000000ull - dt);
-        atomicMax(&p.ctl->prof[20], (dt << 16) | blockIdx.x);
-        atomicMax(&p.ctl->prof[21], (unsigned long long)cnt);
-        atomicMax(&p.ctl->prof[22], qh_prof_acc[2]);
-        atomicMax(&p.ctl->prof[23], qh_prof_acc[6]);
-        if (blockIdx.x < 1024) {
-            unsigned smid;
-            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-            unsigned long long *rec = qh_prof_cta[blockIdx.x];
-            rec[0] = dt;
-            rec[1] = smid;
-            rec[2] = (unsigned long long)first;
-            rec[3] = (unsigned long long)cnt;
-            rec[4] = (unsigned long long)exact_o;
-            rec[5] = (unsigned long long)exact_c;
-            rec[6] = qh_prof_acc[2];
-            rec[7] = qh_prof_acc[4];
-        }
-    }
-#endif
     return true;
 }
 
@@ -1646,7 +1487,6 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
     q.cur = cur;
     q.src = src;
     q.L = L;
-    QH_TL(r + 1, 0);
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
     const unsigned lt = lanemask_lt();
@@ -1659,7 +1499,6 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             pipe_drain<P>(p, gI, gC);
             return false;
         }
-        if (kt == 0) QH_TL(r + 1, 1);
         tile_reset(sm);
         const TileRec &R = desc_of(sm, kt);
         const int valid = R.valid, np = R.np, nItems = R.nItems;
@@ -1789,9 +1628,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         pipe_refill<P>(p, q, kt, s, gI);
     }
     __syncthreads();
-    QH_TL(r + 1, 2);
     if (sm.run.node >= 0) flush_run<P>(p, 2, T, exact_c);
-    QH_TL(r + 1, 3);
     return true;
 }
 
@@ -1993,9 +1830,6 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
 // --------------------------------------------------------------------------
 template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(Params p) {
     RoundSmem<P> &sm = round_smem<P>();
-#ifdef QH_PROFILE
-    if (blockIdx.x == 0 && threadIdx.x == 0) qh_ctl_prof = p.ctl->prof;
-#endif
     unsigned phase = 0;
     int exact_o = 0, exact_c = 0;
     long long surv = 0;
@@ -2010,9 +1844,6 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     stamp(p.ctl, 0);
     if (blockIdx.x == 0) {
         prep<P>(p);
-#ifdef QH_PROFILE
-        tl_reset();
-#endif
     }
     if (!grid_sync(p.ctl, phase, p.spinLimit)) goto out;
     stamp(p.ctl, 1);
@@ -2022,9 +1853,6 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
     stamp(p.ctl, 2);
 
     phase_round0<P>(p, gI, gC, exact_o, exact_c, surv);
-#ifdef QH_PROFILE
-    if (threadIdx.x == 0) atomicMax(&p.ctl->prof[26], global_ns() - __ldcg(&p.ctl->tphase[2]));
-#endif
     if (threadIdx.x == 0 && surv) {
         atomicAdd((unsigned long long *)&p.ctl->live[0], (unsigned long long)surv);
         atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
@@ -2034,15 +1862,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         const int role = grid_arrive(p.ctl, phase, p.spinLimit);
         if (role < 0) goto out;
         if (role == 1) {  // the last CTA builds the first level
-#ifdef QH_PROFILE
-            const unsigned long long tb0 = global_ns();
-            QH_TL(1, 5);
-#endif
             build_level0<P>(p);
-#ifdef QH_PROFILE
-            if (threadIdx.x == 0) p.ctl->prof[27] = global_ns() - tb0;
-            QH_TL(1, 4);
-#endif
             if (!grid_release(p.ctl, phase)) goto out;
         }
     }
@@ -2058,9 +1878,6 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
             break;
         }
         phase_round<P>(p, gI, gC, r, S, L, cur, exact_o, exact_c, surv);
-#ifdef QH_PROFILE
-        if (threadIdx.x == 0 && r <= 1) atomicMax(&p.ctl->prof[26 + 2 * r], global_ns() - __ldcg(&p.ctl->tphase[2 + r]));
-#endif
         if (threadIdx.x == 0 && surv) {
             atomicAdd((unsigned long long *)&p.ctl->live[min(r, MAX_GEN - 1)], (unsigned long long)surv);
             atomicAdd((unsigned long long *)&p.ctl->gridWritten, (unsigned long long)surv);
@@ -2070,15 +1887,7 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         const int role = grid_arrive(p.ctl, phase, p.spinLimit);
         if (role < 0) goto out;
         if (role == 1) {  // the last CTA builds the next level
-#ifdef QH_PROFILE
-            const unsigned long long tb0 = global_ns();
-            QH_TL(r + 1, 5);
-#endif
             build_level<P>(p, r);
-#ifdef QH_PROFILE
-            if (threadIdx.x == 0 && r <= 1) p.ctl->prof[27 + 2 * r] = global_ns() - tb0;
-            QH_TL(r + 1, 4);
-#endif
             if (!grid_release(p.ctl, phase)) goto out;
         }
         stamp(p.ctl, 3 + r);

@@ -1,5 +1,6 @@
-"""Block-size variants of the grid-wide kernel, the cutover range and the
-autotuner: every setting gives the oracle's hull and live counts."""
+"""Kernel variants of the grid-wide rounds (block size x points per thread),
+the cutover range and the autotuner: every setting gives the oracle's hull and
+per-generation live counts."""
 import numpy as np
 import pytest
 
@@ -7,6 +8,8 @@ import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
+
+VARIANTS = [(256, 16), (256, 8), (128, 16), (128, 8)]
 
 
 def _dev(a):
@@ -17,34 +20,48 @@ def _dev(a):
 
 @pytest.mark.parametrize("name", ["square", "disk", "circle", "degenerate"])
 @pytest.mark.parametrize("mode", ["quad", "chord"])
-def test_block_128_matches_oracle(qh, name, mode):
+def test_variants_match_oracle(qh, name, mode):
     p = synth.make(name, 300_000, seed=5)
+    want, live = oracle.quickhull(p, mode)
+    d = _dev(p)
     plan = qh.Plan(len(p), 1, mode=qh.MODE_QUAD if mode == "quad" else qh.MODE_CHORD)
-    plan.set_block(128)
-    t = plan.tuning()
-    assert t["threads_per_block"] == 128 and t["items_per_thread"] == 16 and t["cutover"] >= 2048
-    for cut in (2048, 3072, 4096):
-        plan.set_tuning(cut)
-        got = qh.hull2d(_dev(p), plan).cpu().numpy()
-        st = plan.stats()
-        want, live = oracle.quickhull(p, mode)
-        assert np.array_equal(got, want), cut
-        assert st["device_status"] == 0
-        assert st["live"] == live.tolist(), cut
+    for threads, ipt in VARIANTS:
+        plan.set_block(threads)
+        plan.set_items_per_thread(ipt)
+        t = plan.tuning()
+        assert t["threads_per_block"] == threads and t["items_per_thread"] == ipt
+        for cut in sorted({threads * ipt, 3072, 4096}):
+            if cut < threads * ipt:
+                continue
+            plan.set_tuning(cut)
+            got = qh.hull2d(d, plan).cpu().numpy()
+            st = plan.stats()
+            assert np.array_equal(got, want), (threads, ipt, cut)
+            assert st["device_status"] == 0
+            assert st["live"] == live.tolist(), (threads, ipt, cut)
     plan.close()
 
 
-def test_cutover_range_follows_block_size(qh):
+def test_cutover_range_follows_tile(qh):
     plan = qh.Plan(10_000, 1)
+    t = plan.tuning()
+    assert (t["threads_per_block"], t["items_per_thread"]) == (256, 16)
     with pytest.raises(qh.QhError):
-        plan.set_tuning(2048)  # below the 4096-point tile of the 256-thread kernel
-    plan.set_block(128)
+        plan.set_tuning(2048)  # below the 4096-point tile of 256 threads x 16 points
+    plan.set_items_per_thread(8)
     plan.set_tuning(2048)
     assert plan.tuning()["cutover"] == 2048
-    plan.set_block(256)  # raises the cutover to the tile
-    assert plan.tuning()["cutover"] == 4096
+    plan.set_block(128)
+    plan.set_tuning(1024)
+    assert plan.tuning()["cutover"] == 1024
+    plan.set_items_per_thread(16)  # raises the cutover to the 2048-point tile
+    assert plan.tuning()["cutover"] == 2048
+    with pytest.raises(qh.QhError):
+        plan.set_tuning(4097)
     with pytest.raises(qh.QhError):
         plan.set_block(192)
+    with pytest.raises(qh.QhError):
+        plan.set_items_per_thread(4)
     plan.close()
 
 
@@ -53,7 +70,7 @@ def test_autotune_single_set(qh):
     plan = qh.Plan(len(p), 1)
     d = _dev(p)
     t = plan.autotune(d, reps=2)
-    assert t["threads_per_block"] in (128, 256)
+    assert (t["threads_per_block"], t["items_per_thread"]) in VARIANTS
     assert t["threads_per_block"] * t["items_per_thread"] <= t["cutover"] <= 4096
     assert t["grid_ctas_per_sm"] >= 1
     assert np.array_equal(qh.hull2d(d, plan).cpu().numpy(), oracle.hull2d(p))
@@ -67,7 +84,7 @@ def test_autotune_batched(qh):
     plan = qh.Plan(len(p), 200)
     d, doff = _dev(p), torch.from_numpy(off).cuda()
     t = plan.autotune(d, doff, reps=1)
-    assert t["threads_per_block"] in (128, 256)
+    assert (t["threads_per_block"], t["items_per_thread"]) in VARIANTS
     out, counts = qh.hull2d_batched(d, doff, plan)
     out, counts = out.cpu().numpy(), counts.cpu().numpy()
     want_out, want_counts = oracle.hull2d_batched(p, off)
