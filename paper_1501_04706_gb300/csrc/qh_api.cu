@@ -39,6 +39,8 @@ struct qh_plan_s {
     int *levelBase = nullptr;
     int maxLevels = 0;
     SmallRec *small = nullptr;
+    SmallRec *pack = nullptr;
+    long long *packOff = nullptr;
     int maxSmall = 0;
     int *bigList[2] = {nullptr, nullptr};
     long long *vstart[2] = {nullptr, nullptr};
@@ -90,6 +92,8 @@ void plan_free(qh_plan p) {
     cudaFree(p->tnodes);
     cudaFree(p->levelBase);
     cudaFree(p->small);
+    cudaFree(p->pack);
+    cudaFree(p->packOff);
     cudaFree(p->bigList[0]);
     cudaFree(p->bigList[1]);
     cudaFree(p->vstart[0]);
@@ -145,6 +149,8 @@ qh_status plan_alloc(qh_plan p) {
     QH_ALLOC(p->tnodes, p->maxTNodes);
     QH_ALLOC(p->levelBase, p->maxLevels + 2);
     QH_ALLOC(p->small, p->maxSmall);
+    QH_ALLOC(p->pack, p->maxSmall);
+    QH_ALLOC(p->packOff, p->maxSmall);
     QH_ALLOC(p->bigList[0], p->maxBig + 1);
     QH_ALLOC(p->bigList[1], p->maxBig + 1);
     QH_ALLOC(p->vstart[0], p->maxBig + 2);
@@ -194,6 +200,8 @@ Params make_params(qh_plan pl, const float *points, const long long *offsets, lo
     p.levelBase = pl->levelBase;
     p.maxLevels = pl->maxLevels;
     p.small = pl->small;
+    p.pack = pl->pack;
+    p.packOff = pl->packOff;
     p.maxSmall = pl->maxSmall;
     p.spinLimit = pl->dbgSpin > 0 ? pl->dbgSpin : SPIN_LIMIT;
     p.maxBig = pl->maxBig;
@@ -519,7 +527,7 @@ qh_status qh_plan_get_stats(qh_plan plan, qh_stats *out) {
     out->device_status = err == 0u ? 0 : (err & E_ARG) ? QH_ERR_INVALID_ARG : (err & E_TIMEOUT) ? QH_ERR_TIMEOUT
                                      : (err & E_CAPACITY) ? QH_ERR_CAPACITY : QH_ERR_INTERNAL;
     out->global_rounds = c.rounds;
-    out->small_problems = c.nSmall + c.nSmallInst;
+    out->small_problems = c.nSmall + c.nPack + c.nSmallInst;
     out->nodes = c.nNodes;
     out->big_sets = c.nBig;
     int last = -1;

@@ -1,12 +1,16 @@
 // Block-level parts of segmented QuickHull.
 //
 // finish_kernel  one thread block per small problem: a segment of at most
-//                `cut` points left by the grid-wide rounds, or a whole set of at
-//                most FIN_MAX points.  The block runs the remaining generations
-//                of Sec. 4.4 with all state in shared memory: per point the id
-//                of its segment; per live segment its place in the CCW list of
-//                segment heads; per generation the farthest point of each new
-//                segment and the classification against the two new edges.
+//                `cut` points left by the grid-wide rounds, a pack of up to
+//                PACK_SEGS segments of at most PACK_MAX points each (all from
+//                one level, so they share their generations), or a whole set of
+//                at most FIN_MAX points.  The block runs the remaining
+//                generations of Sec. 4.4 with all state in shared memory: per
+//                point the id of its segment; per live segment its place in the
+//                CCW list of segment heads (a pack lists each segment's chord
+//                h -> e, the end marked as a boundary); per generation the
+//                farthest point of each new segment and the classification
+//                against the two new edges.
 // emit_kernel    one block per set: walks the binary tree of segments built by
 //                the grid-wide rounds (each big segment (h, e) split at its
 //                farthest point c into (h, c), (c, e)), computes the output
@@ -21,17 +25,23 @@ constexpr int FM = FIN_MAX;
 constexpr unsigned short NONE16 = 0xffffu;
 
 struct OrdE {
-    unsigned short head, live, c, pad;  // head point, live segment id (or NONE16), its farthest point
+    unsigned short head, live, c, bnd;  // head point, live segment id (or NONE16), its farthest point;
+                                        // bnd: the end of a packed segment's chord
 };
+constexpr int ORDCAP = FM + 2 * PACK_SEGS + 8;  // heads: one per point, plus every chord's two ends
 
 static_assert(FM % FIN_NT == 0, "the live list is split into FM / FIN_NT entries per thread");
 constexpr int FIN_PER = FM / FIN_NT;
 
 struct FinSmem {
-    float2 pxy[FM + 2];
+    float2 pxy[FM + 2 * PACK_SEGS];  // the points, then the chord ends
     unsigned short seg[FM];  // per point: live segment / child code, NONE16 = discarded
     unsigned short lst[FM];  // the points still live (any order); nLive of them
-    OrdE ordA[FM + 8], ordB[FM + 8];
+    OrdE ordA[ORDCAP], ordB[ORDCAP];
+    unsigned short memStart[PACK_SEGS + 1];  // pack: first point of every segment
+    const int *gidx;         // solo segment: original index of every point
+    int gmode;               // point -> original index: 0 identity (set), 1 gidx, 2 pack
+    int mem0, nMem, packBuf; // pack: first segment in the pack queue, segments, live buffer
     unsigned short lpos[FM];  // live segment -> position in the ord list
     unsigned cnt2[FM];        // per live segment: packed child counts (low: first child, high: second)
     unsigned maxLo[2 * FM];   // per child: largest lower distance bound (orderable key)
@@ -43,6 +53,19 @@ struct FinSmem {
     unsigned short poly[4];
     Ext wext[FIN_NT / 32];
 };
+
+// Original index (local to its set) of problem point k.
+__device__ __forceinline__ int fin_gidx(const Params &p, const FinSmem &s, int k) {
+    if (s.gmode == 0) return k;
+    if (s.gmode == 1) return __ldg(&s.gidx[k]);
+    int lo = 0, hi = s.nMem;  // the packed segment holding k: memStart[lo] <= k < memStart[lo + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s.memStart[mid] <= k) lo = mid; else hi = mid;
+    }
+    const SmallRec *R = &p.pack[s.mem0 + lo];
+    return __ldg(&p.id[s.packBuf][__ldg(&R->pstart) + (k - s.memStart[lo])]);
+}
 
 __device__ __forceinline__ Cand shfl_c(const Cand &c, int src) {
     Cand o;
@@ -100,7 +123,7 @@ __device__ __forceinline__ bool fin_right_of(const FinSmem &s, int u, int v, flo
 // (pass 2), rebuild of the CCW head list and of the live segments, relabelling.
 template <typename P>
 __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial, OrdE *&ord, OrdE *&ordN,
-                               const int *gidx, int gen, int &exact_o, int &exact_c) {
+                               int gen, int &exact_o, int &exact_c) {
     const int S = s.S, nOrd = s.nOrd;
     const int nch = initial ? s.K : 2 * S;
     for (int c = threadIdx.x; c < nch; c += FIN_NT) {
@@ -187,7 +210,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
         DistIv<P> dq = dist_interval(orient_approx(e, q.x, q.y));
         const P thr = (P)fkey_inv(s.maxLo[c]);
         if (!(dq.hi >= thr)) continue;
-        const int qi = gidx ? __ldg(&gidx[k]) : k;
+        const int qi = fin_gidx(p, s, k);
         unsigned short cur = s.best[c];
         for (int it = 0; it < 1 << 20; it++) {
             bool mine;
@@ -195,7 +218,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
                 mine = true;
             } else {
                 const float2 w = s.pxy[cur];
-                const int wi = gidx ? __ldg(&gidx[cur]) : (int)cur;
+                const int wi = fin_gidx(p, s, cur);
                 DistIv<P> dw = dist_interval(orient_approx(e, w.x, w.y));
                 mine = farther(e, b.x, b.y, q.x, q.y, qi, dq, w.x, w.y, wi, dw, exact_c);
             }
@@ -258,7 +281,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
         }
         int tot;
         const int x = block_excl_scan<int, FIN_NT>((w << 16) + __popc(km), s.scan, tot);
-        if (!initial && (tot >> 16) > FM + 4) {  // guard: at most one head per point plus the chord ends
+        if (!initial && (tot >> 16) > ORDCAP - 8) {  // guard: at most one head per point plus the chord ends
             if (threadIdx.x == 0) {
                 set_err(p.ctl, E_INTERNAL);
                 s.S = 0;
@@ -277,7 +300,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
                 o.head = s.poly[c];
                 o.live = s.newId[c];
                 o.c = o.live != NONE16 ? s.best[c] : NONE16;
-                o.pad = 0;
+                o.bnd = 0;
                 ordN[c] = o;
                 if (o.live != NONE16) s.lpos[o.live] = (unsigned short)c;
             }
@@ -295,7 +318,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
                     n.head = wch ? o.c : o.head;
                     n.live = s.newId[2 * j + wch];
                     n.c = n.live != NONE16 ? s.best[2 * j + wch] : NONE16;
-                    n.pad = 0;
+                    n.bnd = 0;
                     ordN[np] = n;
                     if (n.live != NONE16) s.lpos[n.live] = (unsigned short)np;
                     np++;
@@ -354,6 +377,8 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
         s.cLocal = -1;
         s.nonfinite = 0;
         s.degenerate = 0;
+        s.gmode = isNode ? 1 : 0;
+        s.gidx = gidx;
     }
     __syncthreads();
     Ext ex;
@@ -392,11 +417,11 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
             a.head = (unsigned short)m;
             a.live = 0;
             a.c = (unsigned short)max(s.cLocal, 0);
-            a.pad = 0;
+            a.bnd = 0;
             b.head = (unsigned short)(m + 1);
             b.live = NONE16;
             b.c = NONE16;
-            b.pad = 0;
+            b.bnd = 0;
             ord[0] = a;
             ord[1] = b;
             s.lpos[0] = 0;
@@ -453,16 +478,17 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
             }
             return;
         }
-        fin_generation<P>(p, s, m, true, ord, ordN, nullptr, 0, exact_o, exact_c);
+        fin_generation<P>(p, s, m, true, ord, ordN, 0, exact_o, exact_c);
         gen = 1;
     }
     const int genLimit = gen + m + 4;  // every generation removes at least one point per live segment
     while (s.S > 0) {
-        if (gen > genLimit || ld_volatile(&p.ctl->err) != 0u) {
+        // one decision for the whole block: another block may set the error word meanwhile
+        if (__syncthreads_or(gen > genLimit || (threadIdx.x == 0 && ld_volatile(&p.ctl->err) != 0u))) {
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             return;
         }
-        fin_generation<P>(p, s, m, false, ord, ordN, gidx, gen, exact_o, exact_c);
+        fin_generation<P>(p, s, m, false, ord, ordN, gen, exact_o, exact_c);
         gen++;
     }
     const int nOrd = s.nOrd;
@@ -485,22 +511,167 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     __syncthreads();
 }
 
+// Pack k: the packed segments whose weight offsets lie in [k PACK_B,
+// (k + 1) PACK_B), all of one level, solved as one problem.  Every segment
+// enters the CCW head list as its chord h -> e (e marked as a boundary);
+// the generations then treat the live segments of all of them together, and
+// each segment's inner vertices are the heads between its h and its e.
+template <typename P> __device__ void fin_solve_pack(const Params &p, FinSmem &s, long long k, int &exact_o,
+                                                     int &exact_c) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        const long long n = p.ctl->nPack, lo = k * PACK_B, hi = lo + PACK_B;
+        long long a = 0, b = n;  // first offset >= lo
+        while (a < b) {
+            const long long mid = (a + b) >> 1;
+            if (__ldcg(&p.packOff[mid]) < lo) a = mid + 1; else b = mid;
+        }
+        long long c = a, d = n;  // first offset >= hi
+        while (c < d) {
+            const long long mid = (c + d) >> 1;
+            if (__ldcg(&p.packOff[mid]) < hi) c = mid + 1; else d = mid;
+        }
+        s.mem0 = (int)a;
+        s.nMem = (int)(c - a);
+        s.gmode = 2;
+        s.gidx = nullptr;
+    }
+    __syncthreads();
+    const int a = s.mem0, nm = s.nMem;
+    if (nm <= 0) return;
+    if (nm > PACK_SEGS) {  // guard: the weights bound a pack to PACK_SEGS segments
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        return;
+    }
+    const int cnt = threadIdx.x < nm ? __ldg(&p.pack[a + threadIdx.x].count) : 0;
+    int m;
+    const int st = block_excl_scan<int, FIN_NT>(cnt, s.scan, m);
+    const int level = __ldg(&p.pack[a].level), buf = level & 1;  // level r lives in buffer r & 1
+    if (threadIdx.x < nm) s.memStart[threadIdx.x] = (unsigned short)st;
+    if (threadIdx.x == 0) {
+        s.memStart[nm] = (unsigned short)m;
+        s.packBuf = buf;
+        s.nLive = m;
+        s.nOrd = 2 * nm;
+        s.S = nm;
+        atomicAdd((unsigned long long *)&p.ctl->smallPoints, (unsigned long long)m);
+    }
+    for (int i = threadIdx.x; i < nm; i += FIN_NT) s.newId[i] = NONE16;  // farthest point of segment i
+    if (m < 1 || m > FM) {
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        return;
+    }
+    __syncthreads();
+    // the points, segment by segment (one warp per segment), and the chord ends
+    for (int i = wp; i < nm; i += FIN_NT / 32) {
+        const SmallRec *R = &p.pack[a + i];
+        const int c0 = __ldg(&R->count), ps = __ldg(&R->pstart), cIdx = __ldg(&R->cIdx), b0 = s.memStart[i];
+        for (int j = lane; j < c0; j += 32) {
+            s.pxy[b0 + j] = __ldg(&p.xy[buf][ps + j]);
+            s.seg[b0 + j] = (unsigned short)i;
+            s.lst[b0 + j] = (unsigned short)(b0 + j);
+            if (__ldg(&p.id[buf][ps + j]) == cIdx) s.newId[i] = (unsigned short)(b0 + j);
+        }
+        if (lane == 0) {
+            const long long setOff = p.inst[__ldg(&R->inst)].off;
+            s.pxy[m + 2 * i] = __ldg(&p.pts[setOff + __ldg(&R->hIdx)]);
+            s.pxy[m + 2 * i + 1] = __ldg(&p.pts[setOff + __ldg(&R->eIdx)]);
+        }
+    }
+    __syncthreads();
+    OrdE *ord = s.ordA, *ordN = s.ordB;
+    bool ok = true;
+    for (int i = threadIdx.x; i < nm; i += FIN_NT) {
+        const unsigned short c = s.newId[i];
+        ok &= c != NONE16;
+        OrdE h, e;
+        h.head = (unsigned short)(m + 2 * i);
+        h.live = (unsigned short)i;
+        h.c = c == NONE16 ? 0 : c;
+        h.bnd = 0;
+        e.head = (unsigned short)(m + 2 * i + 1);
+        e.live = NONE16;
+        e.c = NONE16;
+        e.bnd = 1;
+        ord[2 * i] = h;
+        ord[2 * i + 1] = e;
+        s.lpos[i] = (unsigned short)(2 * i);
+    }
+    if (!__syncthreads_and(ok)) {  // a segment's farthest point is one of its own points
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        return;
+    }
+    int gen = level + 1;
+    const int genLimit = gen + m + 4;
+    while (s.S > 0) {
+        // one decision for the whole block: another block may set the error word meanwhile
+        if (__syncthreads_or(gen > genLimit || (threadIdx.x == 0 && ld_volatile(&p.ctl->err) != 0u))) {
+            if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+            return;
+        }
+        fin_generation<P>(p, s, m, false, ord, ordN, gen, exact_o, exact_c);
+        gen++;
+    }
+    const int nOrd = s.nOrd;
+    if (nOrd > m + 2 * nm) {  // guard: the output never exceeds the points and the chord ends
+        if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
+        __syncthreads();
+        return;
+    }
+    // positions of every segment's h (entry after a boundary) and e (its boundary)
+    unsigned short *posH = s.lpos;
+    unsigned *posE = s.cnt2;
+    const int per = (nOrd + FIN_NT - 1) / FIN_NT;
+    const int qb = min(nOrd, (int)threadIdx.x * per), qe = min(nOrd, qb + per);
+    int nb = 0;
+    for (int q = qb; q < qe; q++) nb += ord[q].bnd;
+    int tot;
+    const int mb = block_excl_scan<int, FIN_NT>(nb, s.scan, tot);
+    int mm = mb;
+    for (int q = qb; q < qe; q++) {
+        if (ord[q].bnd) {
+            posE[mm++] = q;
+        } else if (q == 0 || ord[q - 1].bnd) {
+            posH[mm] = (unsigned short)q;
+        }
+    }
+    __syncthreads();
+    mm = mb;
+    for (int q = qb; q < qe; q++) {
+        if (ord[q].bnd) {
+            mm++;
+        } else if (!(q == 0 || ord[q - 1].bnd) && mm < nm) {
+            const int ps = __ldg(&p.pack[a + mm].pstart);
+            p.vscratch[ps + q - posH[mm] - 1] = fin_gidx(p, s, ord[q].head);
+        }
+    }
+    for (int i = threadIdx.x; i < nm; i += FIN_NT) {
+        const int inner = (int)posE[i] - (int)posH[i] - 1;
+        p.pack[a + i].cIdx = inner;                       // inner vertices, for the copy pass
+        p.tnodes[__ldg(&p.pack[a + i].tree)].val = inner + 1;  // the leaf's vertices
+    }
+    __syncthreads();
+}
+
 template <typename P> __global__ void __launch_bounds__(FIN_NT, 1) finish_kernel(Params p) {
     extern __shared__ __align__(16) unsigned char fin_smem_raw[];
     FinSmem &s = *reinterpret_cast<FinSmem *>(fin_smem_raw);
     if (p.ctl->err != 0u) return;
     const int nSI = p.ctl->nSmallInst, nSN = p.ctl->nSmall;
+    const long long nPk = (p.ctl->packW + PACK_B - 1) / PACK_B;  // packs (some of them may be empty)
     int exact_o = 0, exact_c = 0;
     for (;;) {
         if (threadIdx.x == 0) s.ticket = (int)atomicAdd(&p.ctl->finTicket, 1u);
         __syncthreads();
-        const int w = s.ticket;
+        const long long w = s.ticket;
         __syncthreads();
-        if (w >= nSI + nSN) break;
+        if (w >= nSI + nSN + nPk) break;
         if (w < nSI)
             fin_solve<P>(p, s, false, p.smallInst[w], exact_o, exact_c);
+        else if (w < nSI + nSN)
+            fin_solve<P>(p, s, true, (int)(w - nSI), exact_o, exact_c);
         else
-            fin_solve<P>(p, s, true, w - nSI, exact_o, exact_c);
+            fin_solve_pack<P>(p, s, w - nSI - nSN, exact_o, exact_c);
     }
     unsigned long long eo = (unsigned long long)exact_o, ec = (unsigned long long)exact_c;
     for (int d = 16; d >= 1; d >>= 1) {
@@ -697,9 +868,9 @@ __global__ void __launch_bounds__(EMIT_NT) emit_kernel(Params p) {
 // The inner vertices of every small segment after its head.
 __global__ void copy_kernel(Params p) {
     if (p.ctl->err != 0u) return;
-    const int nSN = p.ctl->nSmall;
-    for (int w = blockIdx.x; w < nSN; w += gridDim.x) {
-        const SmallRec *R = &p.small[w];
+    const int nSN = p.ctl->nSmall, nPk = p.ctl->nPack;
+    for (int w = blockIdx.x; w < nSN + nPk; w += gridDim.x) {
+        const SmallRec *R = w < nSN ? &p.small[w] : &p.pack[w - nSN];
         const int inner = R->cIdx, count = R->count;
         const Inst *I = &p.inst[R->inst];
         const int o = p.tnodes[R->tree].val;

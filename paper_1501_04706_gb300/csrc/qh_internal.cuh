@@ -33,6 +33,14 @@ constexpr int TILE = NT * IPT;     // points per tile
 constexpr int TILE_MIN = 128 * 8;  // smallest tile of the compiled variants (sizes the plans)
 constexpr int FIN_NT = 512;        // threads per CTA of the block finisher
 constexpr int FIN_MAX = 4096;      // largest problem the block finisher holds in shared memory
+// Small segments of at most PACK_MAX points are finished many at a time: each
+// weighs its points plus PACK_W, and the segments of one level whose weight
+// offsets fall in the same span of PACK_B form one problem (a pack), so a pack
+// holds at most FIN_MAX points and FIN_MAX / PACK_W segments.
+constexpr int PACK_MAX = 1024;
+constexpr int PACK_W = 16;
+constexpr int PACK_B = FIN_MAX - PACK_MAX - PACK_W;
+constexpr int PACK_SEGS = FIN_MAX / PACK_W;
 constexpr int MAX_GEN = 512;       // generations tracked in the statistics (deeper ones add to the last)
 constexpr int MAX_STAMPS = 64;     // grid-phase timestamps kept in the statistics
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // polls (with back-off) before a wait gives up
@@ -124,7 +132,9 @@ struct alignas(128) Ctl {
     long long L;         // points of the current round
     long long tiles;     // tiles of the current round
     int nLevels, nNodes; // levels and TNodes of the segment tree
-    int nSmall;          // small-segment queue length
+    int nSmall;          // small-segment queue length (segments finished one per block)
+    int nPack;           // packed small-segment queue length
+    long long packW;     // weight offset past the last packed segment
     unsigned finTicket;
     int rounds;          // grid-wide rounds run after the initial split
     long long bigPoints;     // points of the sets tiled by the grid-wide kernel
@@ -161,7 +171,9 @@ struct Params {
     int maxTNodes;
     int *levelBase;            // first TNode of every level (maxLevels + 1 entries)
     int maxLevels;
-    SmallRec *small;           // small-segment queue
+    SmallRec *small;           // small-segment queue (one block each)
+    SmallRec *pack;            // small segments finished in packs, in weight-offset order
+    long long *packOff;        // their weight offsets (non-decreasing)
     int maxSmall;
     unsigned spinLimit;        // polls of a grid-barrier wait before it gives up
     int *bigList[2];

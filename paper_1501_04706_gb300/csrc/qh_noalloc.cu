@@ -59,6 +59,8 @@ constexpr size_t NA_SIZES[] = {
     sizeof(TNode) * NA_TNODES,       // tnodes
     sizeof(int) * (NA_LEVELS + 2),   // levelBase
     sizeof(SmallRec) * NA_SMALL,     // small
+    sizeof(SmallRec) * NA_SMALL,     // pack
+    sizeof(long long) * NA_SMALL,    // packOff
     sizeof(Ctl),                     // ctl
 };
 constexpr int NA_NBUF = sizeof(NA_SIZES) / sizeof(NA_SIZES[0]);
@@ -141,8 +143,10 @@ Params na_params(const DeviceScratch &d, const float *points, long long n, int *
     p.levelBase = reinterpret_cast<int *>(b[17]);
     p.maxLevels = (int)NA_LEVELS;
     p.small = reinterpret_cast<SmallRec *>(b[18]);
+    p.pack = reinterpret_cast<SmallRec *>(b[19]);
+    p.packOff = reinterpret_cast<long long *>(b[20]);
     p.maxSmall = (int)NA_SMALL;
-    p.ctl = reinterpret_cast<Ctl *>(b[19]);
+    p.ctl = reinterpret_cast<Ctl *>(b[21]);
     p.spinLimit = SPIN_LIMIT;
     p.cut = FIN_MAX;
     return p;

@@ -655,6 +655,8 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
         p.ctl->nNodes = 0;
         p.ctl->nLevels = 0;
         p.ctl->nSmall = 0;
+        p.ctl->nPack = 0;
+        p.ctl->packW = 0;
     }
     __threadfence();
 }
@@ -1654,51 +1656,64 @@ __device__ void build_biglist(const Params &p, int first, int count, int dstBuf)
     long long *scr = sm.scanTmp;
     const int per = (count + NT - 1) / NT;
     const int b = min(count, threadIdx.x * per), e = min(count, b + per);
-    long long nb = 0, np = 0, ns = 0;
+    // big segments (next round), small ones finished alone, small ones packed
+    long long nb = 0, np = 0, ns = 0, nk = 0, wk = 0;
     for (int k = b; k < e; k++) {
         const Node *N = &p.nodes[first + k];
-        const int kind = __ldcg(&N->kind);
+        const int kind = __ldcg(&N->kind), cnt = __ldcg(&N->count);
         if (kind == K_BIG) {
             nb++;
-            np += __ldcg(&N->count);
+            np += cnt;
         } else if (kind == K_SMALL) {
-            ns++;
+            if (cnt <= PACK_MAX) {
+                nk++;
+                wk += cnt + PACK_W;
+            } else {
+                ns++;
+            }
         }
     }
-    long long totB, totP, totS;
+    long long totB, totP, totS, totK, totW;
     long long xb = block_excl_scan<long long, NT>(nb, scr, totB);
     long long xp = block_excl_scan<long long, NT>(np, scr, totP);
     long long xs = block_excl_scan<long long, NT>(ns, scr, totS);
-    const long long s0 = __ldcg(&p.ctl->nSmall);
-    if (totB > p.maxBig || s0 + totS > p.maxSmall) {
+    long long xk = block_excl_scan<long long, NT>(nk, scr, totK);
+    long long xw = block_excl_scan<long long, NT>(wk, scr, totW);
+    const long long s0 = __ldcg(&p.ctl->nSmall), k0 = __ldcg(&p.ctl->nPack);
+    // this level's packs start at a fresh pack, so a pack's segments share their level
+    const long long w0 = (__ldcg(&p.ctl->packW) + PACK_B - 1) / PACK_B * PACK_B;
+    if (totB > p.maxBig || s0 + totS > p.maxSmall || k0 + totK > p.maxSmall) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return;
     }
     int *bl = p.bigList[dstBuf];
     long long *vs = p.vstart[dstBuf];
     xs += s0;
+    xk += k0;
+    xw += w0;
     for (int k = b; k < e; k++) {
         const int q = first + k;
         const Node *N = &p.nodes[q];
-        const int kind = __ldcg(&N->kind);
+        const int kind = __ldcg(&N->kind), cnt = __ldcg(&N->count);
         if (kind == K_BIG) {
             __stcg(&bl[xb], q);
             __stcg(&vs[xb], xp);
             xb++;
-            xp += __ldcg(&N->count);
+            xp += cnt;
         } else if (kind == K_SMALL) {
-            SmallRec r;
-            r.hIdx = __ldcg(&N->h.idx);
-            r.eIdx = __ldcg(&N->e.idx);
-            r.cIdx = __ldcg(&N->c.idx);
-            r.count = __ldcg(&N->count);
-            r.pstart = (int)__ldcg(&N->pstart);
-            r.level = __ldcg(&N->level);
-            r.inst = __ldcg(&N->inst);
-            r.tree = __ldcg(&N->tree);
-            SmallRec *d = &p.small[xs++];
-            __stcg(reinterpret_cast<int4 *>(d), make_int4(r.hIdx, r.eIdx, r.cIdx, r.count));
-            __stcg(reinterpret_cast<int4 *>(d) + 1, make_int4(r.pstart, r.level, r.inst, r.tree));
+            const int4 w0r = make_int4(__ldcg(&N->h.idx), __ldcg(&N->e.idx), __ldcg(&N->c.idx), cnt);
+            const int4 w1r = make_int4((int)__ldcg(&N->pstart), __ldcg(&N->level), __ldcg(&N->inst),
+                                       __ldcg(&N->tree));
+            SmallRec *d;
+            if (cnt <= PACK_MAX) {
+                __stcg(&p.packOff[xk], xw);
+                xw += cnt + PACK_W;
+                d = &p.pack[xk++];
+            } else {
+                d = &p.small[xs++];
+            }
+            __stcg(reinterpret_cast<int4 *>(d), w0r);
+            __stcg(reinterpret_cast<int4 *>(d) + 1, w1r);
         }
     }
     __syncthreads();
@@ -1709,6 +1724,8 @@ __device__ void build_biglist(const Params &p, int first, int count, int dstBuf)
         p.ctl->tiles = (totP + TILE - 1) / TILE;
         p.ctl->cur = dstBuf;
         p.ctl->nSmall = (int)(s0 + totS);
+        p.ctl->nPack = (int)(k0 + totK);
+        if (totK) p.ctl->packW = w0 + totW;
     }
     __threadfence();
     __syncthreads();
