@@ -43,7 +43,6 @@ def _set_points(n: int) -> None:
         N_POINTS = int(n)
         WORKLOAD = (f"disk-{n}: {n:,} points i.i.d. uniform in the unit disk (r = sqrt(U), angle = 2 pi U), "
                     "seed 0 (profiling size, not the benchmark workload)")
-CPU_SAMPLE = 10_000_000
 
 
 def _peaks():
@@ -133,35 +132,34 @@ def _barrier(ws: int):
 
 
 def run_reference(args, ws, rank):
-    """The reference arm: the CPU oracle, timed on the host cores."""
+    """The reference arm: the CPU oracle on the whole workload, timed on all host cores (the oracle's
+    monotone chain on contiguous chunks in threads, then on the union of the chunk hulls; same output)."""
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     import synth
 
     pts = synth.disk(N_POINTS, seed=0)
-    sample = pts[:2_000_000]
-    oracle.build()
+    oracle.build_parallel()
+    cores = oracle.host_threads()
     for _ in range(args.warmup):
-        oracle.hull2d(sample)
+        oracle.hull2d_parallel(pts, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.hull2d(sample)
-    dt = (time.perf_counter() - t0) / args.steps
-    value = len(sample) / dt / 1e6
+        oracle.hull2d_parallel(pts, cores)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = len(pts) / dt / 1e6
+    sample = (f"whole workload ({len(pts):,} points) per step: the oracle's monotone chain with exact predicates "
+              f"on {cores} contiguous chunks in {cores} threads, then on the union of the chunk hulls")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "first 2,000,000 points of the workload per step"},
-        "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
-                         "sample": "monotone-chain oracle, first 2,000,000 points of the workload per step"},
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-    _ = np
 
 
 def main():
@@ -278,8 +276,10 @@ def main():
         res = qh.hull2d_host(host, plan, host_out)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _reduce_max(e2e_s, ws, device)
+    # qh_hull2d_host reads back the count with the first min(n, 65536) indices, then any indices beyond
+    eager = min(N_POINTS, 65536)
     e2e = {"value": ws * N_POINTS / e2e_s / 1e6, "unit": "Mpts/s", "h2d_bytes_per_step": 8 * N_POINTS,
-           "d2h_bytes_per_step": 4 + 4 * len(res), "ms_per_step": e2e_s * 1e3}
+           "d2h_bytes_per_step": 4 + 4 * eager + 4 * max(0, len(res) - eager), "ms_per_step": e2e_s * 1e3}
 
     extras = {}
     cpu = None
@@ -289,14 +289,21 @@ def main():
         import oracle
 
         oracle.build()
+        oracle.build_parallel()
+        cores = oracle.host_threads()
         t0 = time.perf_counter()
-        want = oracle.hull2d(pts[:CPU_SAMPLE])
-        cpu_s = time.perf_counter() - t0
-        cpu = {"value": CPU_SAMPLE / cpu_s / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
-               "sample": f"monotone-chain oracle on the first {CPU_SAMPLE:,} points of the workload, one pass"}
         full = oracle.hull2d(pts)
+        cpu1_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        full_par = oracle.hull2d_parallel(pts, cores)
+        cpun_s = time.perf_counter() - t0
+        cpu = {"value": N_POINTS / cpun_s / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+               "sample": (f"the whole workload ({N_POINTS:,} points), one pass: the oracle's monotone chain on "
+                          f"{cores} contiguous chunks in {cores} threads, then on the union of the chunk hulls"),
+               "same_output_as_single_thread": bool(np.array_equal(full_par, full)),
+               "single_thread": {"value": N_POINTS / cpu1_s / 1e6, "unit": "Mpts/s", "cores": 1,
+                                 "sample": f"the whole workload ({N_POINTS:,} points), one pass"}}
         parity = bool(np.array_equal(out[:h].cpu().numpy(), full))
-        _ = want
         # plain FP64 form, same workload
         plan64 = qh.Plan(N_POINTS, 1, prec=qh.PREC_F64)
         for _ in range(3):
@@ -344,6 +351,15 @@ def main():
             b.record(stream)
         torch.cuda.synchronize(device)
         msb = sum(a.elapsed_time(b) for a, b in eb) / len(eb)
+        # whole-path algorithmic bytes of the batch: the grid kernel's (16 B per point of the sets it tiles,
+        # 12 B per live point its rounds read or write), 12 B per point the block finisher reads (whole small
+        # sets and small segments), 4 B per output index
+        stb = planb.stats()
+        hb = int(bc.sum().item())
+        alg_b = (16 * stb["grid_points"] + 12 * (stb["grid_read"] + stb["grid_written"]) + 12 * stb["small_points"]
+                 + 4 * hb)
+        gbs_b = alg_b / (msb * 1e-3) / 1e9
+        peak_b, peak_kind_b = _peaks()
         # the same sets, one plain-FP64 call per set on one stream
         nsets = len(boff) - 1
         plan1 = qh.Plan(int(np.max(np.diff(boff))), 1, prec=qh.PREC_F64)
@@ -372,7 +388,11 @@ def main():
                              "sets": nsets, "points": int(len(bp)), "launch": launch, "autotuned": tuned,
                              "per_instance_fp64": {"value": len(bp) / (msi * 1e-3) / 1e6, "unit": "Mpts/s",
                                                    "ms": msi, "calls": nsets, "same_hulls_as_batched": same},
-                             "speedup_vs_per_instance_fp64": msi / msb}
+                             "speedup_vs_per_instance_fp64": msi / msb,
+                             "roofline": {"bound": "hbm", "achieved": gbs_b, "peak": peak_b, "unit": "GB/s",
+                                          "frac": gbs_b / peak_b, "algorithmic_bytes": alg_b,
+                                          "peak_kind": f"{peak_kind_b} copy bandwidth",
+                                          "scope": "whole batched call (grid kernel, finisher, emit, copy)"}}
         plan1.close()
         planb.close()
 

@@ -140,3 +140,54 @@ def quickhull(points, mode: str = "quad", max_gen: int = 4096, mutation: int = 0
         raise OracleError(st)
     g = min(ngen.value, max_gen)
     return out[: cnt.value].copy(), live[:g].copy()
+
+
+# ---------------------------------------------------------------------------
+# All-core timing build (the CPU baseline of bench.py): the same source plus a
+# driver that hulls contiguous chunks in threads and then the union of the
+# chunk hulls; its output is hull2d's output.
+# ---------------------------------------------------------------------------
+_SRC_PAR = os.path.join(_HERE, "qh_oracle_parallel.c")
+_par_lib: list = []
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the all-core driver (includes qh_oracle.c unchanged); return the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "liboracle_par.so")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAR))
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
+        os.close(fd)
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-pthread",
+               "-DQHO_MUTATION=0", "-o", tmp, _SRC_PAR, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def host_threads() -> int:
+    """Threads the all-core driver uses: the cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def hull2d_parallel(points, threads: int | None = None) -> np.ndarray:
+    """hull2d's result, computed on `threads` host threads (default: all cores)."""
+    if not _par_lib:
+        lib = ctypes.CDLL(build_parallel())
+        lib.qho_hull2d_parallel.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int]
+        lib.qho_hull2d_parallel.restype = ctypes.c_int
+        _par_lib.append(lib)
+    p = _points(points)
+    n = p.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    cnt = ctypes.c_int64(0)
+    st = _par_lib[0].qho_hull2d_parallel(p.ctypes.data, n, out.ctypes.data, ctypes.byref(cnt),
+                                         int(threads or host_threads()))
+    if st != 0:
+        raise OracleError(st)
+    return out[: cnt.value].copy()
