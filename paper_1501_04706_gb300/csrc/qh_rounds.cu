@@ -139,6 +139,7 @@ template <typename P> struct RoundSmem {
     int base[4];   // this tile's first output rank in each slot's child
     int fflag[2];  // this tile is the last of part A / part B's parent
     long long scanTmp[NWARP + 1];
+    long long scan5[5][NWARP + 1];  // level build: five prefix sums at once
     Ext wext[NWARP];
     ICand<P> wbest[NWARP][4];
     unsigned mthr[4];  // parent merge: largest lower-bound key per child
@@ -1647,86 +1648,147 @@ __device__ __forceinline__ int node_kind(int count, int cut) {
     return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
 }
 
-// List the big segments of ring entries [first, first + count) for the next
-// round (exclusive prefix of their sizes) and queue the small ones for the
-// block finisher.
-template <typename P>
-__device__ void build_biglist(const Params &p, int first, int count, int dstBuf) {
-    RoundSmem<P> &sm = round_smem<P>();
-    long long *scr = sm.scanTmp;
-    const int per = (count + NT - 1) / NT;
-    const int b = min(count, threadIdx.x * per), e = min(count, b + per);
-    // big segments (next round), small ones finished alone, small ones packed
-    long long nb = 0, np = 0, ns = 0, nk = 0, wk = 0;
-    for (int k = b; k < e; k++) {
-        const Node *N = &p.nodes[first + k];
-        const int kind = __ldcg(&N->kind), cnt = __ldcg(&N->count);
-        if (kind == K_BIG) {
-            nb++;
-            np += cnt;
-        } else if (kind == K_SMALL) {
-            if (cnt <= PACK_MAX) {
-                nk++;
-                wk += cnt + PACK_W;
-            } else {
-                ns++;
-            }
-        }
+// Five exclusive prefix sums over the CTA in one pass (three barriers instead
+// of three per sum); totals in tot.
+__device__ __forceinline__ void block_excl_scan5(long long (&v)[5], long long (&tot)[5],
+                                                 long long (*scr)[NWARP + 1]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) inc[c] = warp_incl_scan(v[c]);
+    if (lane == 31) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) scr[c][w] = inc[c];
     }
-    long long totB, totP, totS, totK, totW;
-    long long xb = block_excl_scan<long long, NT>(nb, scr, totB);
-    long long xp = block_excl_scan<long long, NT>(np, scr, totP);
-    long long xs = block_excl_scan<long long, NT>(ns, scr, totS);
-    long long xk = block_excl_scan<long long, NT>(nk, scr, totK);
-    long long xw = block_excl_scan<long long, NT>(wk, scr, totW);
-    const long long s0 = __ldcg(&p.ctl->nSmall), k0 = __ldcg(&p.ctl->nPack);
-    // this level's packs start at a fresh pack, so a pack's segments share their level
-    const long long w0 = (__ldcg(&p.ctl->packW) + PACK_B - 1) / PACK_B * PACK_B;
-    if (totB > p.maxBig || s0 + totS > p.maxSmall || k0 + totK > p.maxSmall) {
-        if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
-        return;
-    }
-    int *bl = p.bigList[dstBuf];
-    long long *vs = p.vstart[dstBuf];
-    xs += s0;
-    xk += k0;
-    xw += w0;
-    for (int k = b; k < e; k++) {
-        const int q = first + k;
-        const Node *N = &p.nodes[q];
-        const int kind = __ldcg(&N->kind), cnt = __ldcg(&N->count);
-        if (kind == K_BIG) {
-            __stcg(&bl[xb], q);
-            __stcg(&vs[xb], xp);
-            xb++;
-            xp += cnt;
-        } else if (kind == K_SMALL) {
-            const int4 w0r = make_int4(__ldcg(&N->h.idx), __ldcg(&N->e.idx), __ldcg(&N->c.idx), cnt);
-            const int4 w1r = make_int4((int)__ldcg(&N->pstart), __ldcg(&N->level), __ldcg(&N->inst),
-                                       __ldcg(&N->tree));
-            SmallRec *d;
-            if (cnt <= PACK_MAX) {
-                __stcg(&p.packOff[xk], xw);
-                xw += cnt + PACK_W;
-                d = &p.pack[xk++];
-            } else {
-                d = &p.small[xs++];
-            }
-            __stcg(reinterpret_cast<int4 *>(d), w0r);
-            __stcg(reinterpret_cast<int4 *>(d) + 1, w1r);
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            const long long x = lane < NWARP ? scr[c][lane] : 0ll;
+            const long long xi = warp_incl_scan(x);
+            if (lane < NWARP) scr[c][lane] = xi - x;
+            if (lane == NWARP - 1) scr[c][NWARP] = xi;
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __stcg(&vs[totB], totP);
-        p.ctl->S = (int)totB;
-        p.ctl->L = totP;
-        p.ctl->tiles = (totP + TILE - 1) / TILE;
-        p.ctl->cur = dstBuf;
-        p.ctl->nSmall = (int)(s0 + totS);
-        p.ctl->nPack = (int)(k0 + totK);
-        if (totK) p.ctl->packW = w0 + totW;
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        v[c] = scr[c][w] + inc[c] - v[c];
+        tot[c] = scr[c][NWARP];
     }
+    __syncthreads();
+}
+
+// Per-thread tallies of a level's new segments: big ones (and their points)
+// for the next round, small ones finished alone, small ones packed (and their
+// pack weight).
+struct LevelTally {
+    long long v[5];  // big, big points, solo small, packed small, pack weight
+};
+__device__ __forceinline__ void tally_child(LevelTally &t, int kind, int cnt) {
+    if (kind == K_BIG) {
+        t.v[0]++;
+        t.v[1] += cnt;
+    } else if (kind == K_SMALL) {
+        if (cnt <= PACK_MAX) {
+            t.v[3]++;
+            t.v[4] += cnt + PACK_W;
+        } else {
+            t.v[2]++;
+        }
+    }
+}
+
+// Where a level's lists go: running positions of this thread after the scan.
+struct LevelCursor {
+    long long xb, xp, xs, xk, xw;
+    int *bl;
+    long long *vs;
+};
+
+// Scan the tallies and check the list capacities; false (uniform) on overflow.
+// The level's packs start at a fresh pack, so a pack's segments share their level.
+template <typename P>
+__device__ __forceinline__ bool level_lists_open(const Params &p, LevelTally &t, long long (&tot)[5], int dstBuf,
+                                                 long long s0, long long k0, long long pw, LevelCursor &c) {
+    RoundSmem<P> &sm = round_smem<P>();
+    block_excl_scan5(t.v, tot, sm.scan5);
+    if (tot[0] > p.maxBig || s0 + tot[2] > p.maxSmall || k0 + tot[3] > p.maxSmall) {
+        if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
+        return false;
+    }
+    const long long w0 = (pw + PACK_B - 1) / PACK_B * PACK_B;
+    c.xb = t.v[0];
+    c.xp = t.v[1];
+    c.xs = s0 + t.v[2];
+    c.xk = k0 + t.v[3];
+    c.xw = w0 + t.v[4];
+    c.bl = p.bigList[dstBuf];
+    c.vs = p.vstart[dstBuf];
+    return true;
+}
+
+// Enter new segment q of the level in its list (a big one for the next round,
+// a small one in the solo or the packed queue).
+__device__ __forceinline__ void level_list_put(const Params &p, LevelCursor &c, int q, int kind, int cnt, int hIdx,
+                                               int eIdx, int cIdx, long long pstart, int level, int inst, int tree) {
+    if (kind == K_BIG) {
+        __stcg(&c.bl[c.xb], q);
+        __stcg(&c.vs[c.xb], c.xp);
+        c.xb++;
+        c.xp += cnt;
+    } else if (kind == K_SMALL) {
+        SmallRec *d;
+        if (cnt <= PACK_MAX) {
+            __stcg(&p.packOff[c.xk], c.xw);
+            c.xw += cnt + PACK_W;
+            d = &p.pack[c.xk++];
+        } else {
+            d = &p.small[c.xs++];
+        }
+        __stcg(reinterpret_cast<int4 *>(d), make_int4(hIdx, eIdx, cIdx, cnt));
+        __stcg(reinterpret_cast<int4 *>(d) + 1, make_int4((int)pstart, level, inst, tree));
+    }
+}
+
+// Publish the level's list sizes for the next round (thread 0).
+__device__ __forceinline__ void level_lists_close(const Params &p, const long long (&tot)[5], int dstBuf,
+                                                  long long s0, long long k0, long long pw) {
+    if (threadIdx.x == 0) {
+        const long long w0 = (pw + PACK_B - 1) / PACK_B * PACK_B;
+        __stcg(&p.vstart[dstBuf][tot[0]], tot[1]);
+        p.ctl->S = (int)tot[0];
+        p.ctl->L = tot[1];
+        p.ctl->tiles = (tot[1] + TILE - 1) / TILE;
+        p.ctl->cur = dstBuf;
+        p.ctl->nSmall = (int)(s0 + tot[2]);
+        p.ctl->nPack = (int)(k0 + tot[3]);
+        if (tot[3]) p.ctl->packW = w0 + tot[4];
+    }
+}
+
+// List the new segments of ring entries [first, first + count) (level 0).
+template <typename P>
+__device__ void build_biglist(const Params &p, int first, int count, int dstBuf) {
+    const int per = (count + NT - 1) / NT;
+    const int b = min(count, threadIdx.x * per), e = min(count, b + per);
+    const long long s0 = __ldcg(&p.ctl->nSmall), k0 = __ldcg(&p.ctl->nPack), pw = __ldcg(&p.ctl->packW);
+    LevelTally t = {{0, 0, 0, 0, 0}};
+    for (int k = b; k < e; k++) {
+        const Node *N = &p.nodes[first + k];
+        tally_child(t, __ldcg(&N->kind), __ldcg(&N->count));
+    }
+    long long tot[5];
+    LevelCursor c;
+    if (!level_lists_open<P>(p, t, tot, dstBuf, s0, k0, pw, c)) return;
+    for (int k = b; k < e; k++) {
+        const int q = first + k;
+        const Node *N = &p.nodes[q];
+        level_list_put(p, c, q, __ldcg(&N->kind), __ldcg(&N->count), __ldcg(&N->h.idx), __ldcg(&N->e.idx),
+                       __ldcg(&N->c.idx), __ldcg(&N->pstart), __ldcg(&N->level), __ldcg(&N->inst),
+                       __ldcg(&N->tree));
+    }
+    level_lists_close(p, tot, dstBuf, s0, k0, pw);
     __threadfence();
     __syncthreads();
 }
@@ -1794,32 +1856,44 @@ template <typename P> __device__ __noinline__ void build_level0(const Params &p)
 }
 
 // Level r from the big segments of level r - 1 (ring slot (r - 1) & 1): each
-// (h, e) with farthest point c becomes (h, c) and (c, e) in slot r & 1.
+// (h, e) with farthest point c becomes (h, c) and (c, e) in slot r & 1, and
+// the new segments go to their lists in the same pass.  Thread t takes a
+// contiguous range of parents, so one scan of the per-thread tallies gives
+// every list position; the second visit of a parent re-reads its record (an
+// L2 hit) instead of the children just written.
 template <typename P> __device__ __noinline__ void build_level(const Params &p, int r) {
     const int S = __ldcg(&p.ctl->S);
     const int cur = __ldcg(&p.ctl->cur);
     const int base = __ldcg(&p.ctl->nNodes);
+    const long long s0 = __ldcg(&p.ctl->nSmall), k0 = __ldcg(&p.ctl->nPack), pw = __ldcg(&p.ctl->packW);
     if ((long long)base + 2ll * S > p.maxTNodes || 2ll * S > p.slotCap || r + 1 > p.maxLevels) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return;
     }
     const int slot = (r & 1) * p.slotCap;
     const int *bl = p.bigList[cur];
-    for (int j = threadIdx.x; j < S; j += NT) {
+    const int per = (S + NT - 1) / NT;
+    const int jb = min(S, (int)threadIdx.x * per), je = min(S, jb + per);
+    LevelTally t = {{0, 0, 0, 0, 0}};
+    for (int j = jb; j < je; j++) {
         const int q = __ldcg(&bl[j]);
-        Node *Q = &p.nodes[q];
+        const Node *Q = &p.nodes[q];
         const Cand h = ldcg_cand(&Q->h), e = ldcg_cand(&Q->e), c = ldcg_cand(&Q->c);
+        const Cand c0 = ldcg_cand(&Q->chC[0]), c1 = ldcg_cand(&Q->chC[1]);
         const long long ps = __ldcg(&Q->pstart);
-        const int cnt = __ldcg(&Q->count), buf = __ldcg(&Q->buf), inst = __ldcg(&Q->inst);
-        __stcg(&p.tnodes[__ldcg(&Q->tree)].child, base + 2 * j);
+        const int cnt = __ldcg(&Q->count), buf = __ldcg(&Q->buf), inst = __ldcg(&Q->inst), tree = __ldcg(&Q->tree);
+        const int cc0 = __ldcg(&Q->chCount[0]), cc1 = __ldcg(&Q->chCount[1]);
+        __stcg(&p.tnodes[tree].child, base + 2 * j);
+#pragma unroll
         for (int w = 0; w < 2; w++) {
             Node *N = &p.nodes[slot + 2 * j + w];
-            const int cc = __ldcg(&Q->chCount[w]);
+            const int cc = w ? cc1 : cc0;
+            const int kind = node_kind(cc, p.cut);
             stcg_cand(&N->h, w ? c : h);
             stcg_cand(&N->e, w ? e : c);
-            stcg_cand(&N->c, ldcg_cand(&Q->chC[w]));
+            stcg_cand(&N->c, w ? c1 : c0);
             __stcg(&N->count, cc);
-            __stcg(&N->kind, node_kind(cc, p.cut));
+            __stcg(&N->kind, kind);
             __stcg(&N->pstart, w ? ps + cnt - cc : ps);
             __stcg(&N->buf, buf ^ 1);
             __stcg(&N->inst, inst);
@@ -1829,17 +1903,32 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
             __stcg(&N->chCount[1], 0);
             __stcg(&N->tdone, 0u);
             put_tnode(p, base + 2 * j + w, w ? c.idx : h.idx, inst);
+            tally_child(t, kind, cc);
         }
     }
-    __threadfence();
-    __syncthreads();
+    long long tot[5];
+    LevelCursor lc;
+    if (!level_lists_open<P>(p, t, tot, cur ^ 1, s0, k0, pw, lc)) return;
+    for (int j = jb; j < je; j++) {
+        const Node *Q = &p.nodes[__ldcg(&bl[j])];
+        const int hI = __ldcg(&Q->h.idx), eI = __ldcg(&Q->e.idx), cI = __ldcg(&Q->c.idx);
+        const int c0I = __ldcg(&Q->chC[0].idx), c1I = __ldcg(&Q->chC[1].idx);
+        const long long ps = __ldcg(&Q->pstart);
+        const int cnt = __ldcg(&Q->count), inst = __ldcg(&Q->inst);
+        const int cc0 = __ldcg(&Q->chCount[0]), cc1 = __ldcg(&Q->chCount[1]);
+        level_list_put(p, lc, slot + 2 * j, node_kind(cc0, p.cut), cc0, hI, cI, c0I, ps, r, inst, base + 2 * j);
+        level_list_put(p, lc, slot + 2 * j + 1, node_kind(cc1, p.cut), cc1, cI, eI, c1I, ps + cnt - cc1, r, inst,
+                       base + 2 * j + 1);
+    }
+    level_lists_close(p, tot, cur ^ 1, s0, k0, pw);
     if (threadIdx.x == 0) {
         p.ctl->nNodes = base + 2 * S;
         p.ctl->nLevels = r + 1;
         p.levelBase[r + 1] = base + 2 * S;
         p.ctl->rounds = r;
     }
-    build_biglist<P>(p, slot, 2 * S, cur ^ 1);
+    __threadfence();
+    __syncthreads();
 }
 
 // --------------------------------------------------------------------------
