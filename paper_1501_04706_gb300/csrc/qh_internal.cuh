@@ -195,6 +195,20 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(volatile const unsigned *)p; }
+// Counter arrivals.  Release: the caller's writes, and those of its CTA ordered
+// before it by a CTA barrier, become visible no later than the increment.
+// Acquire (acq_rel): the caller also sees everything released by the earlier
+// increments of the same counter.
+__device__ __forceinline__ unsigned atom_add_release(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ Cand ldcg_cand(const Cand *p) {
     int4 v = __ldcg(reinterpret_cast<const int4 *>(p));
@@ -248,8 +262,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase, unsigned li
     if (threadIdx.x == 0) {
         phase++;
         const unsigned target = phase * gridDim.x;
-        __threadfence();
-        atomicAdd(&ctl->bar, 1u);
+        atom_add_release(&ctl->bar, 1u);
         unsigned it = 0, ns = 32;
         int ok = 1;
         while (ld_acquire(&ctl->bar) < target) {
@@ -265,7 +278,6 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned &phase, unsigned li
             __nanosleep(ns);  // back-off: 32 ns doubling to 256 ns
             ns = ns < 256u ? 2u * ns : ns;
         }
-        __threadfence();
         if (ld_volatile(&ctl->err) != 0u) ok = 0;
         s_ok = ok;
     }
@@ -283,8 +295,7 @@ __device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase, unsigned l
     __syncthreads();
     if (threadIdx.x == 0) {
         phase++;
-        __threadfence();
-        const unsigned d = atomicAdd(&ctl->bar, 1u);
+        const unsigned d = atom_add_acq_rel(&ctl->bar, 1u);  // the leader acquires every arrival's writes
         int role = 0;
         if (d == phase * gridDim.x - 1u) {
             role = 1;
@@ -304,7 +315,6 @@ __device__ __forceinline__ int grid_arrive(Ctl *ctl, unsigned &phase, unsigned l
                 ns = ns < 256u ? 2u * ns : ns;
             }
         }
-        __threadfence();
         if (ld_volatile(&ctl->err) != 0u) role = -1;
         s_role = role;
     }
@@ -316,7 +326,6 @@ __device__ __forceinline__ bool grid_release(Ctl *ctl, unsigned phase) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         st_release(&ctl->gen, phase);
         s_ok = ld_volatile(&ctl->err) == 0u;
     }

@@ -541,14 +541,13 @@ __device__ __noinline__ void flush_run(const Params &p, int kind, long long T, i
     const int nslot = ra.nslot;
     if (threadIdx.x == 32) {
         for (int s = 0; s < nslot; s++) stcg_cand(&p.tbest[4 * ra.first + ra.slotBase + s], ra.best[s].c);
-        __threadfence();
         unsigned *cnt = kind == 1 ? &p.inst[ra.node].done0 : &p.nodes[ra.node].tdone;
-        const unsigned old = atomicAdd(cnt, (unsigned)ra.tiles);
+        // release: this run's record; acquire: the records of the runs counted before
+        const unsigned old = atom_add_acq_rel(cnt, (unsigned)ra.tiles);
         sm.fflag[0] = old + (unsigned)ra.tiles == (unsigned)ra.total;
     }
     __syncthreads();
     if (sm.fflag[0]) {
-        __threadfence();
         merge_runs<P>(p, ra.ta, ra.tb, ra.slotBase0, nslot, ra.edgeOff, T, exact_c);
         if (threadIdx.x < nslot) {
             Cand *dstC = kind == 1 ? &p.inst[ra.node].chC[threadIdx.x] : &p.nodes[ra.node].chC[threadIdx.x];
@@ -659,7 +658,6 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
         p.ctl->nPack = 0;
         p.ctl->packW = 0;
     }
-    __threadfence();
 }
 
 // --------------------------------------------------------------------------
@@ -890,10 +888,9 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         Ext r = sm.wext[0];
         for (int k = 1; k < NWARP; k++) ext_merge(r, sm.wext[k]);
         st_ext(&p.text[segFirst], r);
-        __threadfence();
-        const unsigned prev = atomicAdd(&p.inst[i].done, (unsigned)segTiles);
+        // release: this CTA's partial; acquire: the partials counted before
+        const unsigned prev = atom_add_acq_rel(&p.inst[i].done, (unsigned)segTiles);
         sm.kflag = (prev + (unsigned)segTiles == (unsigned)__ldcg(&p.inst[i].tiles));
-        __threadfence();
     }
     __syncthreads();
     if (!sm.kflag) {
@@ -937,7 +934,6 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
         W.K = K;
         W.iB = iB;
         for (int k = 0; k < 4; k++) W.poly[k] = (k < K || (kind == I_DEGEN && k == 0)) ? poly[k] : no_cand();
-        __threadfence();
     }
     __syncthreads();
 }
@@ -1789,8 +1785,7 @@ __device__ void build_biglist(const Params &p, int first, int count, int dstBuf)
                        __ldcg(&N->tree));
     }
     level_lists_close(p, tot, dstBuf, s0, k0, pw);
-    __threadfence();
-    __syncthreads();
+    __syncthreads();  // the grid release that follows publishes the lists
 }
 
 // A tree node: leaves start with one vertex (their head; a small segment adds
@@ -1927,8 +1922,7 @@ template <typename P> __device__ __noinline__ void build_level(const Params &p, 
         p.levelBase[r + 1] = base + 2 * S;
         p.ctl->rounds = r;
     }
-    __threadfence();
-    __syncthreads();
+    __syncthreads();  // the grid release that follows publishes the level
 }
 
 // --------------------------------------------------------------------------
