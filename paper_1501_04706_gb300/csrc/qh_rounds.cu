@@ -139,9 +139,8 @@ template <typename P> struct RoundSmem {
     int base[4];   // this tile's first output rank in each slot's child
     int fflag[2];  // this tile is the last of part A / part B's parent
     long long scanTmp[NWARP + 1];
-    long long scan5[5][NWARP + 1];  // level build: five prefix sums at once
     Ext wext[NWARP];
-    ICand<P> wbest[NWARP][4];
+    alignas(16) ICand<P> wbest[NWARP][4];  // per-warp bests; the level build's scan scratch between rounds
     unsigned mthr[4];  // parent merge: largest lower-bound key per child
     ICand<P> candq[4][CQ];
     unsigned clsPack[2][NT];     // 4-bit slot of every item of the tile (CLS_NONE: discarded)
@@ -711,8 +710,9 @@ __device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool 
     R.bytes = bytes;
 }
 
-__device__ void resolve_round_tile(const Params &p, TileRec &R, long long t, int S, long long L, int cur, int src) {
-    const long long v0 = t * TILE, v1 = min(v0 + (long long)TILE, L);
+__device__ void resolve_round_tile(const Params &p, TileRec &R, long long t, int S, long long L, int cur, int src,
+                                   int ts) {
+    const long long v0 = t * ts, v1 = min(v0 + (long long)ts, L);
     const long long *vs = p.vstart[cur];
     const int *bl = p.bigList[cur];
     const long long sA = upper_bound_ll(vs, (long long)S + 1, v0) - 1;
@@ -793,6 +793,7 @@ struct TileSeq {
     long long first, step, cnt;
     int kind;  // 0: set tiles (extremes), 1: set tiles with polygon (round 0), 2: round tiles
     int S, cur, src;
+    int ts;    // round tiles: points per tile
     long long L;
 };
 template <typename P> __device__ void resolve_batch(const Params &p, const TileSeq &q, long long k0) {
@@ -802,7 +803,7 @@ template <typename P> __device__ void resolve_batch(const Params &p, const TileS
     if (j < DB && k0 + j < q.cnt) {
         const long long t = q.first + (k0 + j) * q.step;
         if (q.kind == 2)
-            resolve_round_tile(p, desc_of(sm, k0 + j), t, q.S, q.L, q.cur, q.src);
+            resolve_round_tile(p, desc_of(sm, k0 + j), t, q.S, q.L, q.cur, q.src, q.ts);
         else
             resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1, sm.setc);
     }
@@ -1468,13 +1469,34 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
 // --------------------------------------------------------------------------
 // round r >= 1
 // --------------------------------------------------------------------------
+// Points per tile of a grid round over L live points: the full tile, halved
+// (down to TILE_MIN) while every CTA still gets at most one tile, so a short
+// round spreads over more CTAs and each one's tile ends sooner.  Segments of a
+// round hold more than cut >= TILE points, so a smaller tile still meets at
+// most two of them.
+__device__ __forceinline__ int round_tile_points(long long L, long long G) {
+    int ts = TILE;
+    while (ts > TILE_MIN && (L + ts / 2 - 1) / (ts / 2) <= G) ts /= 2;
+    return ts;
+}
+
+// Items j >= jn of every thread are outside a short tile: their slot nibbles
+// read as CLS_NONE.
+__device__ __forceinline__ void mark_unused_items(int jn, unsigned &cp0, unsigned &cp1) {
+    if (jn >= IPT) return;
+    cp0 |= jn >= 8 ? 0u : (0xffffffffu << (4 * jn));
+    if (IPT > 8) cp1 |= jn <= 8 ? 0xffffffffu : (jn >= 16 ? 0u : (0xffffffffu << (4 * (jn - 8))));
+}
+
 template <typename P>
 __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI,
                                          unsigned long long &gC, int r, int S, long long L, int cur, int &exact_o,
                                          int &exact_c, long long &survivors) {
     RoundSmem<P> &sm = round_smem<P>();
     const int src = (r - 1) & 1, dst = r & 1;
-    const long long T = (L + TILE - 1) / TILE, G = gridDim.x;
+    const long long G = gridDim.x;
+    const int ts = round_tile_points(L, G);
+    const long long T = (L + ts - 1) / ts;
     const long long first = chunk_start(blockIdx.x, T, G);
     const long long cnt = chunk_start(blockIdx.x + 1, T, G) - first;
     TileSeq q;
@@ -1485,6 +1507,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
     q.S = S;
     q.cur = cur;
     q.src = src;
+    q.ts = ts;
     q.L = L;
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
@@ -1509,7 +1532,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         if (sm.run.node >= 0 && sm.run.node != R.node[0]) flush_run<P>(p, 2, T, exact_c);  // the previous segment
         if (sm.run.node < 0) {
             const long long vs = R.vstart[0], cn = R.count[0];
-            run_start(sm.run, R.node[0], 2, R.t, 0, 0, vs / TILE, (vs + cn - 1) / TILE, (vs % TILE) != 0 ? 2 : 0);
+            run_start(sm.run, R.node[0], 2, R.t, 0, 0, vs / ts, (vs + cn - 1) / ts, (vs % ts) != 0 ? 2 : 0);
         }
         if (threadIdx.x < 2 * np) {
             const int part = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -1524,11 +1547,15 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         const int dx0 = R.g[0].dx, dx1 = R.g[1].dx, di0 = R.g[0].di, di1 = R.g[1].di;
         const float2 *xs = sm.stage[s].xy;
         const int *is = sm.stage[s].id;
-        // pass 1: strictly right of h->c (first child) or of c->e (second child)
+        // pass 1: strictly right of h->c (first child) or of c->e (second child).
+        // A short tile stops after the groups of items that hold points (jn is
+        // the same in the whole CTA).
+        const int jn = min(IPT, ((nItems + NT - 1) / NT + UNROLL_ITEMS - 1) / UNROLL_ITEMS * UNROLL_ITEMS);
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
         unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi = 0u;
 #pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
+            if (j % UNROLL_ITEMS == 0 && j >= jn) break;
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
             const bool pb = i >= vB;
@@ -1552,6 +1579,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             const int c = classify_exact<P>(s0, s0 + 1, v.x, v.y, lo, hi, exact_o);
             renote_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
+        mark_unused_items(jn, cp0, cp1);
         pass1_commit(sm, cp0, cp1, pc, mlo);
         Node *NA = &p.nodes[R.node[0]];
         Node *NB = &p.nodes[R.node[np == 2 ? 1 : 0]];
@@ -1573,6 +1601,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         bool bad = false;
 #pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
+            if (j % UNROLL_ITEMS == 0 && j >= jn) break;
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
             const int rank = slot_rank(c, wr, lt);
@@ -1619,7 +1648,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             __syncthreads();
             flush_run<P>(p, 2, T, exact_c);
             const long long vs = R.vstart[1], cn = R.count[1];
-            run_start(sm.run, R.node[1], 2, R.t, 2, 2, vs / TILE, (vs + cn - 1) / TILE, 2);
+            run_start(sm.run, R.node[1], 2, R.t, 2, 2, vs / ts, (vs + cn - 1) / ts, 2);
             __syncthreads();
             if (threadIdx.x < 2) sm.run.best[threadIdx.x] = sm.best[2 + threadIdx.x];
             if (threadIdx.x == 0) sm.run.tiles = 1;
@@ -1708,7 +1737,8 @@ template <typename P>
 __device__ __forceinline__ bool level_lists_open(const Params &p, LevelTally &t, long long (&tot)[5], int dstBuf,
                                                  long long s0, long long k0, long long pw, LevelCursor &c) {
     RoundSmem<P> &sm = round_smem<P>();
-    block_excl_scan5(t.v, tot, sm.scan5);
+    static_assert(sizeof(sm.wbest) >= sizeof(long long[5][NWARP + 1]), "scan scratch fits the warp bests");
+    block_excl_scan5(t.v, tot, reinterpret_cast<long long(*)[NWARP + 1]>(&sm.wbest[0][0]));
     if (tot[0] > p.maxBig || s0 + tot[2] > p.maxSmall || k0 + tot[3] > p.maxSmall) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return false;
@@ -1973,7 +2003,8 @@ template <typename P> __global__ void __launch_bounds__(NT, MINB) rounds_kernel(
         if (S == 0) break;
         const long long L = __ldcg(&p.ctl->L);
         const int cur = __ldcg(&p.ctl->cur);
-        if ((L + TILE - 1) / TILE > p.maxTiles) {
+        const int ts = round_tile_points(L, gridDim.x);
+        if ((L + ts - 1) / ts > p.maxTiles) {
             if (blockIdx.x == 0 && threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
             break;
         }
