@@ -137,13 +137,17 @@ qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *
                              int32_t *cutover, int32_t *grid_ctas_per_sm);
 
 /*
- * Autotuner (not in the paper): hulls the caller's input once per candidate setting -- every kernel variant
- * (block size x points per thread), grid CTAs per SM from the occupancy maximum down to half of it, and the
- * cutovers 1024, 2048 and 4096 -- timing `reps` runs of each with CUDA events on `stream`, and keeps the
- * fastest setting in the plan.  offsets == NULL: one set of n points (as qh_hull2d_p); otherwise a CSR batch (as
- * qh_hull2d_batched, n ignored).  Synchronizes the stream; out_idx / out_counts are overwritten by every
- * trial and end up holding the (identical) result of the last.  reps in [1, 64], else
- * QH_ERR_INVALID_ARG; a failing trial's status is returned and the previous best kept.
+ * Autotuner (not in the paper): hulls the caller's input with the plan's current setting (the reference),
+ * then once per candidate setting -- every kernel variant (block size x points per thread), grid CTAs per
+ * SM from the occupancy maximum down to half of it, and every cutover from the variant's tile to 4096 in
+ * steps of 1024 -- and checks on the device that each candidate's output equals the reference's (vertex
+ * counts and every index; the hull is unique).  A candidate that agrees is timed over `reps` runs with
+ * CUDA events on `stream`; the fastest agreeing candidate is kept in the plan.  offsets == NULL: one set
+ * of n points (as qh_hull2d_p); otherwise a CSR batch (as qh_hull2d_batched, n ignored).  Allocates a copy
+ * of the reference output for the duration of the call and synchronizes the stream; out_idx / out_counts
+ * end up holding the result of the last trial.  Errors: QH_ERR_INVALID_ARG (reps outside [1, 64]),
+ * QH_ERR_INTERNAL (some candidate's output differed from the reference; the best agreeing setting is
+ * kept), a failing trial's status (the best setting so far is kept).
  */
 qh_status qh_plan_autotune(qh_plan plan, const float *points, const int64_t *offsets, int32_t num_sets,
                            int64_t n, int32_t *out_idx, int32_t *out_counts, int32_t reps, qh_stream_t stream);

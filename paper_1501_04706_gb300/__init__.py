@@ -106,6 +106,62 @@ def _stream(device=None) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
+TUNE_CACHE_ENV = "QH_TUNE_CACHE"
+_build_id: list = []
+
+
+def library_build_id() -> str:
+    """Content hash of the library's sources: a tuning stored by another build is not reused."""
+    if not _build_id:
+        import hashlib
+
+        h = hashlib.sha256()
+        here = os.path.dirname(os.path.abspath(__file__))
+        csrc = os.path.join(here, "csrc")
+        for f in sorted(os.listdir(csrc)) + [os.path.join("..", "..", "include", "qh.h")]:
+            path = os.path.join(csrc, f)
+            if os.path.isfile(path):
+                with open(path, "rb") as fh:
+                    h.update(fh.read())
+        _build_id.append(h.hexdigest()[:12])
+    return _build_id[0]
+
+
+def tune_cache_key(device_name: str, capability, flags: int, num_sets: int, n: int) -> str:
+    """Key of a stored tuning: GPU, library build and the call's configuration."""
+    return (f"{device_name}|sm{int(capability[0])}{int(capability[1])}|build={library_build_id()}"
+            f"|flags={int(flags)}|sets={int(num_sets)}|n={int(n)}")
+
+
+def tune_cache_load(path: str) -> dict:
+    """The stored tunings (empty when the file is missing or unreadable)."""
+    import json
+
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get("entries", {})
+        return e if isinstance(e, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def tune_cache_store(path: str, key: str, tuning: dict) -> None:
+    """Add one tuning to the file (written to a temporary file, then renamed into place)."""
+    import json
+    import tempfile
+
+    entries = tune_cache_load(path)
+    entries[key] = {k: int(tuning[k]) for k in ("threads_per_block", "items_per_thread", "cutover",
+                                                  "grid_ctas_per_sm")}
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(suffix=".json", dir=d)
+    with os.fdopen(fd, "w") as f:
+        json.dump({"version": 1, "entries": entries}, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Plan:
     """Device scratch for hulls of up to ``max_points`` points in up to ``max_sets`` sets."""
 
@@ -116,6 +172,7 @@ class Plan:
         self.handle = h
         self.max_points = int(max_points)
         self.max_sets = int(max_sets)
+        self.flags = mode | prec
 
     def close(self) -> None:
         if self.handle:
@@ -130,6 +187,7 @@ class Plan:
 
     def set_flags(self, mode: int = MODE_QUAD, prec: int = PREC_F32) -> None:
         _check(load().qh_plan_set_flags(self.handle, mode | prec), "qh_plan_set_flags")
+        self.flags = mode | prec
 
     def set_tuning(self, cutover: int = 4096, timing: bool = False, ctas_per_sm: int = 0) -> None:
         _check(load().qh_plan_set_tuning(self.handle, int(cutover), int(bool(timing)), int(ctas_per_sm)),
@@ -140,7 +198,7 @@ class Plan:
         _check(load().qh_plan_set_block(self.handle, int(threads)), "qh_plan_set_block")
 
     def set_items_per_thread(self, ipt: int) -> None:
-        """Points per thread per tile of the grid-wide kernel: 16 or 8 (a tile is 32 x ipt points)."""
+        """Points per thread per tile of the grid-wide kernel: 16 or 8 (a tile is threads x ipt points)."""
         _check(load().qh_plan_set_items_per_thread(self.handle, int(ipt)), "qh_plan_set_items_per_thread")
 
     def set_debug(self, spin_limit: int = 0, max_tree_nodes: int = 0) -> None:
@@ -154,8 +212,19 @@ class Plan:
         return {"threads_per_block": v[0].value, "items_per_thread": v[1].value, "cutover": v[2].value,
                 "grid_ctas_per_sm": v[3].value}
 
-    def autotune(self, points, offsets=None, out=None, counts=None, reps: int = 3) -> dict:
-        """Time every candidate setting on this input, keep the fastest; returns the chosen tuning."""
+    def apply_tuning(self, t: dict) -> None:
+        """Set block size, points per thread, cutover and grid CTAs per SM from a tuning dict."""
+        self.set_block(int(t["threads_per_block"]))
+        self.set_items_per_thread(int(t["items_per_thread"]))
+        self.set_tuning(int(t["cutover"]), False, int(t["grid_ctas_per_sm"]))
+
+    def autotune(self, points, offsets=None, out=None, counts=None, reps: int = 3, cache: str | None = None) -> dict:
+        """Time every candidate setting on this input (each one's output checked against the plan's current
+        setting on the device), keep the fastest; returns the chosen tuning with ``cached``.
+
+        With a cache file (``cache``, else the ``QH_TUNE_CACHE`` environment variable) the result is stored
+        under a key of GPU name, compute capability, library build, flags, set count and point count, and a
+        later call with the same key applies the stored tuning without timing anything."""
         import torch
 
         pts = _points_tensor(points)
@@ -165,13 +234,25 @@ class Plan:
         else:
             off = offsets.to(device=dev, dtype=torch.int64).contiguous()
             num_sets, off_ptr = off.shape[0] - 1, off.data_ptr()
+        path = cache if cache is not None else os.environ.get(TUNE_CACHE_ENV)
+        key = None
+        if path:
+            key = tune_cache_key(torch.cuda.get_device_name(dev), torch.cuda.get_device_capability(dev),
+                                 self.flags, num_sets, pts.shape[0])
+            hit = tune_cache_load(path).get(key)
+            if hit is not None:
+                self.apply_tuning(hit)
+                return dict(self.tuning(), cached=True)
         if out is None:
             out = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=dev)
         if counts is None:
             counts = torch.empty(max(num_sets, 1), dtype=torch.int32, device=dev)
         _check(load().qh_plan_autotune(self.handle, pts.data_ptr(), off_ptr, num_sets, pts.shape[0], out.data_ptr(),
                                        counts.data_ptr(), int(reps), _stream(dev)), "qh_plan_autotune")
-        return self.tuning()
+        t = self.tuning()
+        if path:
+            tune_cache_store(path, key, t)
+        return dict(t, cached=False)
 
     def stats(self) -> dict:
         s = _Stats()

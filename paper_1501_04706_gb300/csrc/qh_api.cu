@@ -370,21 +370,55 @@ qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *
 qh_status qh_plan_autotune(qh_plan plan, const float *points, const int64_t *offsets, int32_t num_sets, int64_t n,
                            int32_t *out_idx, int32_t *out_counts, int32_t reps, qh_stream_t stream) {
     if (!plan || reps < 1 || reps > 64) return QH_ERR_INVALID_ARG;
+    if (offsets && num_sets <= 0) return num_sets == 0 ? QH_OK : QH_ERR_INVALID_ARG;
+    if (!out_counts || (!offsets && n < 0)) return QH_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     auto call = [&]() -> qh_status {
         return offsets ? qh_hull2d_batched(plan, points, offsets, num_sets, out_idx, out_counts, stream)
                        : qh_hull2d_p(plan, points, n, out_idx, out_counts, stream);
     };
+    const int sets = offsets ? num_sets : 1;
+    long long total = n;
+    if (offsets) {
+        int64_t last = 0;
+        cudaError_t e = cudaMemcpyAsync(&last, offsets + num_sets, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+        total = last;
+    }
+    // The reference: the plan's setting before tuning.  Every candidate's output
+    // must equal it (the hull is unique); a candidate that differs is never chosen.
+    int *ref = nullptr, *refCnt = nullptr;
+    unsigned *diff = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    auto release = [&]() {
+        cudaFree(ref);
+        cudaFree(refCnt);
+        cudaFree(diff);
         if (a) cudaEventDestroy(a);
-        return QH_ERR_CUDA;
+        if (b) cudaEventDestroy(b);
+    };
+    cudaError_t e = cudaMalloc((void **)&ref, sizeof(int) * (size_t)(total > 0 ? total : 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&refCnt, sizeof(int) * (size_t)sets);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&diff, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_status(e);
     }
     const int saveTiming = plan->timing;
     plan->timing = 0;
+    qh_status st = call();
+    if (st == QH_OK && total > 0)
+        e = cudaMemcpyAsync(ref, out_idx, sizeof(int) * (size_t)total, cudaMemcpyDeviceToDevice, s);
+    if (st == QH_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(refCnt, out_counts, sizeof(int) * (size_t)sets, cudaMemcpyDeviceToDevice, s);
+    if (st == QH_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st == QH_OK && e != cudaSuccess) st = cuda_status(e);
     float best = -1.f;
     int bestV = plan->variant, bestCut = plan->cut, bestCtas = plan->ctasPerSm;
-    qh_status st = QH_OK;
+    int rejected = 0;
     const int prec = (plan->flags & QH_PREC_F64) ? 1 : 0;
     for (int v = 0; v < NUM_ROUNDS_VARIANTS && st == QH_OK; v++) {
         const RoundsVariant &V = rounds_variant(v);
@@ -394,7 +428,20 @@ qh_status qh_plan_autotune(qh_plan plan, const float *points, const int64_t *off
                 plan->variant = v;
                 plan->ctasPerSm = ctas;
                 plan->cut = cut;
-                st = call();  // warm-up (first use of the variant, caches)
+                st = call();  // warm-up (first use of the variant, caches), then the check
+                unsigned d = 0u;
+                if (st == QH_OK) {
+                    e = launch_compare_hulls(out_idx, out_counts, ref, refCnt,
+                                             reinterpret_cast<const long long *>(offsets), sets, total, diff, s);
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(&d, diff, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                    if (e != cudaSuccess) st = cuda_status(e);
+                }
+                if (st != QH_OK) break;
+                if (d != 0u) {
+                    rejected++;
+                    continue;
+                }
                 float tot = 0.f;
                 for (int r = 0; r < reps && st == QH_OK; r++) {
                     cudaEventRecord(a, s);
@@ -418,9 +465,9 @@ qh_status qh_plan_autotune(qh_plan plan, const float *points, const int64_t *off
     plan->cut = bestCut;
     plan->ctasPerSm = bestCtas;
     plan->timing = saveTiming;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return st;
+    release();
+    if (st != QH_OK) return st;
+    return rejected ? QH_ERR_INTERNAL : QH_OK;
 }
 
 qh_status qh_hull2d_p(qh_plan plan, const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,

@@ -945,6 +945,43 @@ cudaError_t launch_copy(const Params &p, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Autotuner check: counts the entries in which a trial's output differs from
+// the reference setting's (vertex counts, and every index inside a hull).  Set
+// s of a batch owns out[offsets[s] ..][: counts[s]]; one set: offsets == null.
+__global__ void compare_hulls_kernel(const int *out, const int *cnt, const int *ref, const int *refCnt,
+                                     const long long *offsets, int numSets, long long n, unsigned *diff) {
+    unsigned d = 0u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < numSets; s += stride)
+        d += cnt[s] != refCnt[s];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        int set = 0;
+        long long base = 0;
+        if (offsets) {  // the set holding position i: the last s with offsets[s] <= i
+            int lo = 0, hi = numSets;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (offsets[mid] <= i) lo = mid; else hi = mid;
+            }
+            set = lo;
+            base = offsets[lo];
+        }
+        const int c = refCnt[set];
+        if (i - base < (long long)c && c > 0) d += out[i] != ref[i];
+    }
+    if (d) atomicAdd(diff, d);
+}
+
+cudaError_t launch_compare_hulls(const int *out, const int *cnt, const int *ref, const int *refCnt,
+                                 const long long *offsets, int numSets, long long n, unsigned *diff, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(diff, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const long long work = n > numSets ? n : numSets;
+    const int nb = (int)(work / 256 + 1 < 4096 ? work / 256 + 1 : 4096);
+    compare_hulls_kernel<<<nb, 256, 0, s>>>(out, cnt, ref, refCnt, offsets, numSets, n, diff);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_orient(const float *tri, long long n, int prec, int *sign, int *cert, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int nb = (int)((n + 255) / 256);

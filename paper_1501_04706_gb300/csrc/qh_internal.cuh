@@ -125,7 +125,7 @@ struct alignas(128) Ctl {
     unsigned gen;        // barriers released by their leader (monotonic within a launch)
     unsigned padGen[31];
     int nBig, nSmallInst;
-    int pad0;
+    int setTile;         // points per tile of the extreme-point pass and the initial split
     long long bigTiles;  // tiles over all big sets
     int S;               // big segments of the current round
     int cur;             // bigList buffer of the current round
@@ -417,6 +417,8 @@ cudaError_t launch_finish(const Params &p, int prec, int grid, cudaStream_t s);
 int finish_smem_bytes();
 cudaError_t launch_emit(const Params &p, cudaStream_t s);
 cudaError_t launch_copy(const Params &p, int grid, cudaStream_t s);
+cudaError_t launch_compare_hulls(const int *out, const int *cnt, const int *ref, const int *refCnt,
+                                 const long long *offsets, int numSets, long long n, unsigned *diff, cudaStream_t s);
 cudaError_t launch_check_orient(const float *tri, long long n, int prec, int *sign, int *cert, cudaStream_t s);
 cudaError_t launch_check_dist(const float *quads, long long n, int *sign, cudaStream_t s);
 

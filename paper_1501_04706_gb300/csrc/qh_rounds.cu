@@ -581,10 +581,60 @@ __device__ __forceinline__ void run_start(RunAcc<P> &ra, int node, int nslot, lo
 // --------------------------------------------------------------------------
 // prep: classify sets (CTA 0)
 // --------------------------------------------------------------------------
-template <typename P> __device__ __noinline__ void prep(const Params &p) {
+// Five exclusive prefix sums over the CTA in one pass (three barriers instead
+// of three per sum); totals in tot.
+__device__ __forceinline__ void block_excl_scan5(long long (&v)[5], long long (&tot)[5],
+                                                 long long (*scr)[NWARP + 1]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) inc[c] = warp_incl_scan(v[c]);
+    if (lane == 31) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) scr[c][w] = inc[c];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            const long long x = lane < NWARP ? scr[c][lane] : 0ll;
+            const long long xi = warp_incl_scan(x);
+            if (lane < NWARP) scr[c][lane] = xi - x;
+            if (lane == NWARP - 1) scr[c][NWARP] = xi;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        v[c] = scr[c][w] + inc[c] - v[c];
+        tot[c] = scr[c][NWARP];
+    }
+    __syncthreads();
+}
+
+// The scratch of the five-way scan: the warp-best array, idle outside the tile loops.
+template <typename P> __device__ __forceinline__ long long (*scan5_scratch())[NWARP + 1] {
     RoundSmem<P> &sm = round_smem<P>();
-    long long *scr = sm.scanTmp;
+    static_assert(sizeof(sm.wbest) >= sizeof(long long[5][NWARP + 1]), "scan scratch fits the warp bests");
+    return reinterpret_cast<long long(*)[NWARP + 1]>(&sm.wbest[0][0]);
+}
+
+// Points per tile of the extreme-point pass and the initial split: a single
+// set small enough for the grid spreads over more CTAs with smaller tiles
+// (halved down to TILE_MIN while every CTA still gets at most one); a batch
+// keeps the full tile.
+__device__ __forceinline__ int set_tile_points(const Params &p) {
+    int ts = TILE;
+    if (p.numSets == 1 && !p.offsets) {
+        const long long n = p.nSingle;
+        while (ts > TILE_MIN && (n + ts / 2 - 1) / (ts / 2) <= (long long)gridDim.x) ts /= 2;
+    }
+    return ts;
+}
+
+template <typename P> __device__ __noinline__ void prep(const Params &p) {
     long long carryBig = 0, carrySmall = 0, carryTiles = 0, bigPts = 0, smallPts = 0;
+    const int ts = set_tile_points(p);
     for (int base = 0; base < p.numSets; base += NT) {
         const int i = base + threadIdx.x;
         long long off = 0, n = 0;
@@ -603,18 +653,16 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
             }
             kind = n == 0 ? I_EMPTY : (n <= FIN_MAX ? I_SMALL : I_BIG);
         }
-        const long long tiles = kind == I_BIG ? (n + TILE - 1) / TILE : 0;
-        // packed scan: big count (bits 0..19), small count (20..39), tiles (40..63) would
-        // overflow for large batches, so scan the three quantities separately.
-        long long tb, ts, tt;
-        long long xb = block_excl_scan<long long, NT>(kind == I_BIG ? 1 : 0, scr, tb);
-        long long xs = block_excl_scan<long long, NT>(kind == I_SMALL ? 1 : 0, scr, ts);
-        long long xt = block_excl_scan<long long, NT>(tiles, scr, tt);
-        long long tbp, tsp;
-        block_excl_scan<long long, NT>(kind == I_BIG ? n : 0, scr, tbp);
-        block_excl_scan<long long, NT>(kind == I_SMALL ? n : 0, scr, tsp);
-        bigPts += tbp;
-        smallPts += tsp;
+        const long long tiles = kind == I_BIG ? (n + ts - 1) / ts : 0;
+        // big sets, small sets, tiles, big-set points, small-set points: one five-way scan
+        long long v[5] = {kind == I_BIG ? 1 : 0, kind == I_SMALL ? 1 : 0, tiles, kind == I_BIG ? n : 0,
+                          kind == I_SMALL ? n : 0};
+        long long tot[5];
+        block_excl_scan5(v, tot, scan5_scratch<P>());
+        const long long xb = v[0], xs = v[1], xt = v[2];
+        const long long tb = tot[0], tsm = tot[1], tt = tot[2];
+        bigPts += tot[3];
+        smallPts += tot[4];
         if (i < p.numSets) {
             Inst &I = p.inst[i];
             I.off = off;
@@ -637,7 +685,7 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
             }
         }
         carryBig += tb;
-        carrySmall += ts;
+        carrySmall += tsm;
         carryTiles += tt;
     }
     if (threadIdx.x == 0) {
@@ -645,6 +693,7 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
         if (carryTiles > p.maxTiles) set_err(p.ctl, E_CAPACITY);
         p.ctl->nBig = (int)carryBig;
         p.ctl->nSmallInst = (int)carrySmall;
+        p.ctl->setTile = ts;
         p.ctl->bigTiles = carryTiles;
         p.ctl->bigPoints = bigPts;
         p.ctl->smallPoints = smallPts;
@@ -664,7 +713,8 @@ template <typename P> __device__ __noinline__ void prep(const Params &p) {
 // (binary searches, segment records) of DB tiles overlap; thread 0 then only
 // copies a descriptor and starts its TMA copies.
 // --------------------------------------------------------------------------
-__device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool withPoly, const SetCache &sc) {
+__device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool withPoly, const SetCache &sc,
+                                 int ts) {
     R.t = t;
     R.np = 1;
     R.valid = 1;
@@ -699,8 +749,8 @@ __device__ void resolve_set_tile(const Params &p, TileRec &R, long long t, bool 
         }
     }
     R.lt = t - R.tile0;
-    const long long first = R.lt * TILE;
-    const int c = (int)min((long long)TILE, R.setN - first);
+    const long long first = R.lt * ts;
+    const int c = (int)min((long long)ts, R.setN - first);
     R.nItems = c;
     int sx = 0, si = 0;
     unsigned bytes = 0u;
@@ -805,7 +855,7 @@ template <typename P> __device__ void resolve_batch(const Params &p, const TileS
         if (q.kind == 2)
             resolve_round_tile(p, desc_of(sm, k0 + j), t, q.S, q.L, q.cur, q.src, q.ts);
         else
-            resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1, sm.setc);
+            resolve_set_tile(p, desc_of(sm, k0 + j), t, q.kind == 1, sm.setc, q.ts);
     }
     __syncthreads();
     if (q.kind != 2 && threadIdx.x == 0) {  // cache the set of the batch's last tile
@@ -980,6 +1030,20 @@ __device__ __forceinline__ void renote_item(int j, int c, unsigned klo, unsigned
             if (c == q) mlo[q] = max(mlo[q], klo);
         mhi = max(mhi, khi);
     }
+}
+
+// Items j >= jn of every thread are outside a short tile: their slot nibbles
+// read as CLS_NONE.
+__device__ __forceinline__ void mark_unused_items(int jn, unsigned &cp0, unsigned &cp1) {
+    if (jn >= IPT) return;
+    cp0 |= jn >= 8 ? 0u : (0xffffffffu << (4 * jn));
+    if (IPT > 8) cp1 |= jn <= 8 ? 0xffffffffu : (jn >= 16 ? 0u : (0xffffffffu << (4 * (jn - 8))));
+}
+
+// The item groups of a tile that hold points (the same in the whole CTA): a
+// short tile's loops stop after them.
+__device__ __forceinline__ int item_groups_end(int nItems) {
+    return min(IPT, ((nItems + NT - 1) / NT + UNROLL_ITEMS - 1) / UNROLL_ITEMS * UNROLL_ITEMS);
 }
 
 // Bit k of the result: nibble k of w equals q (an exact zero-nibble test:
@@ -1244,6 +1308,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
     q.cnt = cnt;
     q.kind = 0;
     q.S = q.cur = q.src = 0;
+    q.ts = __ldcg(&p.ctl->setTile);
     q.L = 0;
     tile_extremes_reset(sm);
     pipe_start<P>(p, q, gI);
@@ -1268,7 +1333,7 @@ __device__ __noinline__ bool phase_extremes(const Params &p, unsigned long long 
             segTiles = 0;
         }
         const int nItems = R.nItems, dx = R.g[0].dx;
-        const int base = (int)(R.lt * TILE);
+        const int base = (int)(R.lt * q.ts);
         const float2 *xs = sm.stage[s].xy;
         // pass A: the tile's coordinate extremes (fminf/fmaxf skip NaN, flagged apart)
         float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
@@ -1344,6 +1409,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
     q.cnt = cnt;
     q.kind = 1;
     q.S = q.cur = q.src = 0;
+    q.ts = __ldcg(&p.ctl->setTile);
     q.L = 0;
     tile_reset(sm);
     pipe_start<P>(p, q, gI);
@@ -1379,10 +1445,12 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         const bool hasBot = iB == 2, hasTop = K - iB == 2;
         const float botx = R.poly[1].x, topx = R.poly[(iB + 1) & 3].x;
         const float2 *xs = sm.stage[s].xy;
+        const int jn = item_groups_end(nItems);
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
         unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi = 0u;
 #pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
+            if (j % UNROLL_ITEMS == 0 && j >= jn) break;
             const int i = j * NT + threadIdx.x;
             const bool in = i < nItems;
             const float2 v = xs[i + dx];  // inside the stage for every j; masked below
@@ -1405,13 +1473,14 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             const int c = classify_exact<P>(e0, e1, v.x, v.y, lo, hi, exact_o);
             renote_item(j, c, max(pkey(lo), 1u), max(pkey_up(hi), 1u), cp0, cp1, pc, mlo, mhi);
         }
+        mark_unused_items(jn, cp0, cp1);
         pass1_commit(sm, cp0, cp1, pc, mlo);
         Inst *W = &p.inst[R.inst];
         int *const cursors[4] = {&W->chCount[0], &W->chCount[1], &W->chCount[2], &W->chCount[3]};
         tile_reserve(sm, K, cursors);
         // pass 2: write the survivors, then offer candidates
         const long long off = R.setOff, n = R.setN;
-        const int idBase = (int)(R.lt * TILE);
+        const int idBase = (int)(R.lt * q.ts);
         int wr[4];
         unsigned thr[4];
 #pragma unroll
@@ -1424,6 +1493,7 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         bool bad = false;
 #pragma unroll UNROLL_ITEMS
         for (int j = 0; j < IPT; j++) {
+            if (j % UNROLL_ITEMS == 0 && j >= jn) break;
             const int i = j * NT + threadIdx.x;
             const int c = item_cls(j, cp0, cp1);
             const int rank = slot_rank(c, wr, lt);
@@ -1478,14 +1548,6 @@ __device__ __forceinline__ int round_tile_points(long long L, long long G) {
     int ts = TILE;
     while (ts > TILE_MIN && (L + ts / 2 - 1) / (ts / 2) <= G) ts /= 2;
     return ts;
-}
-
-// Items j >= jn of every thread are outside a short tile: their slot nibbles
-// read as CLS_NONE.
-__device__ __forceinline__ void mark_unused_items(int jn, unsigned &cp0, unsigned &cp1) {
-    if (jn >= IPT) return;
-    cp0 |= jn >= 8 ? 0u : (0xffffffffu << (4 * jn));
-    if (IPT > 8) cp1 |= jn <= 8 ? 0xffffffffu : (jn >= 16 ? 0u : (0xffffffffu << (4 * (jn - 8))));
 }
 
 template <typename P>
@@ -1550,7 +1612,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         // pass 1: strictly right of h->c (first child) or of c->e (second child).
         // A short tile stops after the groups of items that hold points (jn is
         // the same in the whole CTA).
-        const int jn = min(IPT, ((nItems + NT - 1) / NT + UNROLL_ITEMS - 1) / UNROLL_ITEMS * UNROLL_ITEMS);
+        const int jn = item_groups_end(nItems);
         unsigned cp0 = 0u, cp1 = 0u, pc = 0u, um = 0u;
         unsigned mlo[4] = {0u, 0u, 0u, 0u}, mhi = 0u;
 #pragma unroll UNROLL_ITEMS
@@ -1673,37 +1735,6 @@ __device__ __forceinline__ int node_kind(int count, int cut) {
     return count == 0 ? K_LEAF : (count <= cut ? K_SMALL : K_BIG);
 }
 
-// Five exclusive prefix sums over the CTA in one pass (three barriers instead
-// of three per sum); totals in tot.
-__device__ __forceinline__ void block_excl_scan5(long long (&v)[5], long long (&tot)[5],
-                                                 long long (*scr)[NWARP + 1]) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    long long inc[5];
-#pragma unroll
-    for (int c = 0; c < 5; c++) inc[c] = warp_incl_scan(v[c]);
-    if (lane == 31) {
-#pragma unroll
-        for (int c = 0; c < 5; c++) scr[c][w] = inc[c];
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int c = 0; c < 5; c++) {
-            const long long x = lane < NWARP ? scr[c][lane] : 0ll;
-            const long long xi = warp_incl_scan(x);
-            if (lane < NWARP) scr[c][lane] = xi - x;
-            if (lane == NWARP - 1) scr[c][NWARP] = xi;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < 5; c++) {
-        v[c] = scr[c][w] + inc[c] - v[c];
-        tot[c] = scr[c][NWARP];
-    }
-    __syncthreads();
-}
-
 // Per-thread tallies of a level's new segments: big ones (and their points)
 // for the next round, small ones finished alone, small ones packed (and their
 // pack weight).
@@ -1737,8 +1768,7 @@ template <typename P>
 __device__ __forceinline__ bool level_lists_open(const Params &p, LevelTally &t, long long (&tot)[5], int dstBuf,
                                                  long long s0, long long k0, long long pw, LevelCursor &c) {
     RoundSmem<P> &sm = round_smem<P>();
-    static_assert(sizeof(sm.wbest) >= sizeof(long long[5][NWARP + 1]), "scan scratch fits the warp bests");
-    block_excl_scan5(t.v, tot, reinterpret_cast<long long(*)[NWARP + 1]>(&sm.wbest[0][0]));
+    block_excl_scan5(t.v, tot, scan5_scratch<P>());
     if (tot[0] > p.maxBig || s0 + tot[2] > p.maxSmall || k0 + tot[3] > p.maxSmall) {
         if (threadIdx.x == 0) set_err(p.ctl, E_CAPACITY);
         return false;

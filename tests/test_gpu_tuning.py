@@ -77,6 +77,30 @@ def test_autotune_single_set(qh):
     plan.close()
 
 
+def test_autotune_cache_and_reuse(qh, tmp_path):
+    """A tuning stored under the GPU, build and configuration is applied by a later plan without timing."""
+    p = synth.circle(400_000, seed=12)
+    want = oracle.hull2d(p)
+    d = _dev(p)
+    path = str(tmp_path / "tune.json")
+    plan = qh.Plan(len(p), 1)
+    t = plan.autotune(d, reps=1, cache=path)
+    assert t["cached"] is False
+    assert np.array_equal(qh.hull2d(d, plan).cpu().numpy(), want)
+    stored = qh.tune_cache_load(path)
+    assert len(stored) == 1
+    plan.close()
+    plan2 = qh.Plan(len(p), 1)
+    t2 = plan2.autotune(d, reps=1, cache=path)
+    assert t2["cached"] is True
+    assert {k: t2[k] for k in stored[next(iter(stored))]} == stored[next(iter(stored))]
+    assert np.array_equal(qh.hull2d(d, plan2).cpu().numpy(), want)
+    t3 = plan2.autotune(d[:300_000], reps=1, cache=path)  # another configuration: tuned, then stored
+    assert t3["cached"] is False and len(qh.tune_cache_load(path)) == 2
+    assert np.array_equal(qh.hull2d(d[:300_000], plan2).cpu().numpy(), oracle.hull2d(p[:300_000]))
+    plan2.close()
+
+
 def test_autotune_batched(qh):
     import torch
 
