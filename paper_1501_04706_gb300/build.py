@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     """Compile (if sources changed) and return the path of libqh.so.
 
     ``extra`` adds nvcc flags; with ``out_path`` the library (and its objects)
-    go to another file, e.g. for a build with -DQH_PROFILE section counters.
+    go to another file, e.g. for an experiment build with extra defines.
     """
     lib_path = out_path or LIB_PATH
     if out_path is None and not force and not _stale():

@@ -2,8 +2,8 @@
 //
 // orient(u, v, p) = (vx-ux)(py-uy) - (vy-uy)(px-ux): > 0 when p is left of the
 // directed line u->v.  A point is outside a CCW hull edge u->v when it is
-// strictly right (orient < 0), the "right side of the directed line AC and CB"
-// test of Sec. 4.4.3.  Its distance beyond the edge is dist(p) = -orient(u,v,p);
+// strictly right of it (orient < 0): the side test of Sec. 4.4.3 against the
+// two new edges h->c and c->e.  Its distance beyond the edge is dist(p) = -orient(u,v,p);
 // the paper's distance (Sec. 4.4.1) differs from it by the positive factor
 // 1/|uv|, so the farthest point is the same and no division is needed.
 //

@@ -2,7 +2,7 @@
 //
 // Phases (separated by bounded grid barriers):
 //   prep       CTA 0 classifies the sets: empty, small (<= FIN_MAX points, left
-//              to the block finisher) or big (tiled here).
+//              to the block finisher) or big (tiled here), and sizes the tiles.
 //   extremes   per big set, the four extreme points of Sec. 4.2 (lexicographic
 //              min/max of (x, y) and of (y, x), ties to the lower index).  Each
 //              CTA streams a contiguous chunk of tiles and keeps running
@@ -16,12 +16,18 @@
 //              points strictly right of h->c or of c->e (Sec. 4.4.3), compact
 //              them into the two child segments (h, c), (c, e) (Sec. 4.4.2/4.4.4)
 //              and find each child's farthest point (Sec. 4.4.1) in the same
-//              pass; then the last CTA builds the next level of segments.
+//              pass.  The last CTA to reach the grid barrier that ends the
+//              round (its leader) builds the next level of segments and the
+//              lists for the next round and the finisher, then releases the
+//              others.  The rounds end when no big segment is left, at any
+//              depth: the segment tree keeps every level.
 //
 // Memory pipeline: every CTA owns a ring of NS shared-memory stages filled by
 // TMA bulk copies (cp.async.bulk + mbarrier).  Thread 0 resolves the segment
 // descriptors of tile k + NS and starts its copies while the CTA works on tile
-// k, so HBM latency and descriptor lookups overlap the per-tile work.
+// k, so HBM latency and descriptor lookups overlap the per-tile work.  Short
+// rounds (and a single small set) use smaller tiles, so they spread over more
+// CTAs.
 //
 // Compaction is a single pass.  Segments are contiguous ranges of a live
 // buffer and a child never leaves its parent's range: the first child grows
@@ -30,8 +36,11 @@
 // child's cursor, so no tile ever waits for another (a tile-ordered scan would
 // chain the ~600 tiles a persistent grid has in flight; the order of points
 // inside a segment is irrelevant to the method).  The farthest point of each
-// child is exact: each tile stores its own exact best per child, and the last
-// tile of a parent (per-parent tile counter) merges the parent's tile bests.
+// child is exact: every CTA works on a contiguous chunk of tiles, keeps the
+// exact best of each child over its run of tiles of one parent and publishes
+// it once, as a record in the run's first tile; the CTA whose publication
+// completes the parent's tile count merges the parent's records (they sit at
+// the parent's first tile and at the chunk starts inside its range).
 // Segments with at most `cut` points (cut >= TILE) leave the grid-wide rounds
 // for the block finisher, so a tile of a round spans at most two segments.
 #include "qh_internal.cuh"
