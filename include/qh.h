@@ -89,8 +89,8 @@ typedef struct {
 /*
  * qh_plan_create -- allocate a plan for up to max_points points in up to
  * max_sets sets.  flags: QH_MODE_* | QH_PREC_*.  The plan holds roughly
- * 120 bytes of device scratch per point: two nested copies of the live points,
- * and a segment tree, small-segment queue and level table sized for any input
+ * 165 bytes of device scratch per point: two nested copies of the live points,
+ * and a segment tree, small-segment queues and level table sized for any input
  * (a set of n points has at most 2n tree nodes, n small segments and n levels),
  * so no input within max_points exceeds it, however deep the recursion.
  * Errors: QH_ERR_INVALID_ARG (sizes < 1), QH_ERR_CAPACITY (max_points above
@@ -210,7 +210,7 @@ qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int3
  *   points, n, out_idx, out_count, stream: as for qh_hull2d_p.
  *   n must not exceed QH_NOALLOC_MAX_POINTS; larger sets return QH_ERR_CAPACITY
  *   without touching the device.
- * Scratch: one fixed array in the library's device image (about 31 MB on every
+ * Scratch: one fixed array in the library's device image (about 43 MB on every
  * GPU that loads the library, held until the process exits); no cudaMalloc,
  * cudaFree or other allocating call is made.  The first call on a device looks up
  * the array's address for that device (it must come before any stream capture)
