@@ -512,23 +512,25 @@ __device__ __noinline__ void merge_runs(const Params &p, long long ta, long long
             for (int j = 0; j < n; j++) imerge(b, sm.candq[q][j], edgeOff + q, sm, exact_c);
             sm.fin[q] = b.c;
         }
-    } else {  // massive exact ties: reduce all records
-#pragma unroll 1
-        for (int q = 0; q < nslot; q++) {
+    } else {  // massive exact ties: every slot at once, each reduced by its own group of warps
+        const int wps = NWARP / nslot;  // nslot is 2..4 and NWARP >= 4
+        const int q = w / wps, sub = w - q * wps;
+        if (q < nslot) {
             ICand<P> b = no_icand<P>();
-            for (long long r = threadIdx.x; r < nrec; r += NT) {
+#pragma unroll 1
+            for (long long r = (long long)sub * 32 + lane; r < nrec; r += (long long)wps * 32) {
                 int base;
                 const long long tile = rec_tile(r, base);
                 if (tile >= 0) imerge(b, icand_of(sm, edgeOff + q, ldcg_cand(&p.tbest[4 * tile + base + q])), edgeOff + q, sm, exact_c);
             }
 #pragma unroll 1
             for (int d = 16; d >= 1; d >>= 1) imerge(b, shfl_icand(b, lane ^ d), edgeOff + q, sm, exact_c);
-            if (lane == 0) sm.wbest[w][q] = b;
+            if (lane == 0) sm.wbest[w][0] = b;
         }
         __syncthreads();
         if (threadIdx.x < nslot) {
             ICand<P> b = no_icand<P>();
-            for (int k = 0; k < NWARP; k++) imerge(b, sm.wbest[k][threadIdx.x], edgeOff + threadIdx.x, sm, exact_c);
+            for (int k = 0; k < wps; k++) imerge(b, sm.wbest[threadIdx.x * wps + k][0], edgeOff + threadIdx.x, sm, exact_c);
             sm.fin[threadIdx.x] = b.c;
         }
     }
