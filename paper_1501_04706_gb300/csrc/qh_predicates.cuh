@@ -275,13 +275,18 @@ QH_HD bool f32_exact_range(float x) {
 
 QH_HD double xp(float a, float b) { return rmul(double(a), double(b)); }
 
-// sign(sum of s_k a_k b_k), s_k = +-1, exactly (FP32 expansion when in range).
-template <int N>
-QH_HD int product_sum_sign(const float (&a)[N], const float (&b)[N], const int (&sg)[N]) {
+// Every factor zero or in [2^-51, 2^61]: the products' FP32 expansion is exact.
+template <int N> QH_HD bool factors_in_f32_range(const float (&a)[N], const float (&b)[N]) {
     bool in = true;
 #pragma unroll
     for (int k = 0; k < N; k++) in = in && f32_exact_range(a[k]) && f32_exact_range(b[k]);
-    if (in) {
+    return in;
+}
+
+// sign(sum of s_k a_k b_k), s_k = +-1, exactly (FP32 expansion when in range).
+template <int N>
+QH_HD int product_sum_sign(const float (&a)[N], const float (&b)[N], const int (&sg)[N]) {
+    if (factors_in_f32_range(a, b)) {
         float t[2 * N];
 #pragma unroll
         for (int k = 0; k < N; k++) {
@@ -298,11 +303,53 @@ QH_HD int product_sum_sign(const float (&a)[N], const float (&b)[N], const int (
     return expansion_sign(t);
 }
 
+// sign((a1 - a0)(b1 - b0) - (c1 - c0)(d1 - d0)) for floats, decided in FP64
+// where that is certain (*decided = false otherwise).  Used before the FP64
+// expansion only (factors outside the FP32 range): GB300's FP64 rate is a
+// small fraction of its FP32 rate, so in range the FP32 expansion is faster.  A difference of two
+// floats is exact in FP64 unless their exponents lie far apart; TwoSum's error
+// term (exact in round-to-nearest) tells which.  With exact differences, each
+// product is exact when its FMA residue is zero (float differences are
+// multiples of 2^-149, so products cannot underflow, and they cannot overflow);
+// then the sign is the comparison of the two products.  Otherwise l - r is
+// within 2u (|l| + |r|) of the exact value (u = 2^-53), and a bound of 4u,
+// which also covers the rounding of the bound, decides all but near-zero cases.
+QH_HD int diff_products_sign64(float a1, float a0, float b1, float b0, float c1, float c0, float d1, float d0,
+                               bool &decided) {
+    double x[4], e[4];
+    const float hi[4] = {a1, b1, c1, d1}, lo[4] = {a0, b0, c0, d0};
+    bool exactDiff = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        two_sum(double(hi[k]), -double(lo[k]), x[k], e[k]);
+        exactDiff = exactDiff && e[k] == 0.0;
+    }
+    decided = false;
+    if (!exactDiff) return 0;
+    const double l = rmul(x[0], x[1]), r = rmul(x[2], x[3]);
+    if (rfma(x[0], x[1], -l) == 0.0 && rfma(x[2], x[3], -r) == 0.0) {
+        decided = true;
+        return (l > r) - (l < r);
+    }
+    const double det = rsub(l, r);
+    const double err = rmul(radd(l < 0.0 ? -l : l, r < 0.0 ? -r : r), 4.0 * 0x1p-53);
+    if (det > err || -det > err) {
+        decided = true;
+        return det > 0.0 ? 1 : -1;
+    }
+    return 0;
+}
+
 // orient(a,b,c) = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx, exactly.
 QH_HD_COLD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
     const float fa[6] = {bx, bx, ax, by, by, ay};
     const float fb[6] = {cy, ay, cy, cx, ax, cx};
     const int sg[6] = {1, -1, -1, -1, 1, 1};
+    if (!factors_in_f32_range(fa, fb)) {
+        bool decided;
+        const int s64 = diff_products_sign64(bx, ax, cy, ay, by, ay, cx, ax, decided);
+        if (decided) return s64;
+    }
     return product_sum_sign(fa, fb, sg);
 }
 
@@ -312,6 +359,11 @@ QH_HD_COLD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, 
     const float fa[8] = {vx, vx, ux, ux, vy, vy, uy, uy};
     const float fb[8] = {py, qy, py, qy, px, qx, px, qx};
     const int sg[8] = {-1, 1, 1, -1, 1, -1, -1, 1};
+    if (!factors_in_f32_range(fa, fb)) {
+        bool decided;  // the same value as (vy-uy)(px-qx) - (vx-ux)(py-qy)
+        const int s64 = diff_products_sign64(vy, uy, px, qx, vx, ux, py, qy, decided);
+        if (decided) return s64;
+    }
     return product_sum_sign(fa, fb, sg);
 }
 

@@ -150,3 +150,30 @@ def test_host_exact_paths_across_magnitudes(lib):
     got = qh.check_dist_host(q)
     wantd = np.array([dist_sign(t[0:2], t[2:4], t[4:6], t[6:8]) for t in q])
     assert np.array_equal(got, wantd)
+
+
+def test_host_exact_paths_far_apart_exponents(lib):
+    """Nearly and exactly collinear triples on y = x whose coordinates lie up to 2^120
+    apart: some differences are exact in FP64 and some are not, so every stage of
+    the exact fallback (FP64 difference form, product comparison, expansions) is
+    reached; all agree with rational arithmetic."""
+    import paper_1501_04706_gb300 as qh
+
+    rng = np.random.default_rng(13)
+    tri = []
+    for _ in range(600):
+        e = rng.integers(-60, 61, size=3).astype(np.float32)
+        x = ((np.float32(1.0) + rng.random(3).astype(np.float32)) * np.float32(2.0) ** e).astype(np.float32)
+        y = x.copy()
+        k = int(rng.integers(0, 3))
+        if k:
+            y[2] = np.nextafter(y[2], np.float32((-1) ** k * np.inf))
+        tri.append([x[0], y[0], x[1], y[1], x[2], y[2]])
+    tri = np.array(tri, dtype=np.float32)
+    assert np.isfinite(tri).all()
+    sign, _ = qh.check_orient_host(tri, 0)
+    assert np.array_equal(sign, np.array([orient(t[0:2], t[2:4], t[4:6]) for t in tri]))
+    q = np.concatenate([tri, tri[:, 4:6] * np.float32(1.0)], axis=1)
+    q[:, 7] = np.nextafter(q[:, 7], np.float32(np.inf))
+    got = qh.check_dist_host(q)
+    assert np.array_equal(got, np.array([dist_sign(t[0:2], t[2:4], t[4:6], t[6:8]) for t in q]))
