@@ -340,15 +340,42 @@ QH_HD int diff_products_sign64(float a1, float a0, float b1, float b0, float c1,
     return 0;
 }
 
+// The same in FP32 when every difference is exact (TwoSum error zero; always
+// so for coordinates within a factor of two of each other) and zero or in
+// [2^-51, 2^61]: each product is then exactly the sum of its rounded value and
+// its FMA residue (as in the expansions below), so the sign is that of a
+// four-term sum -- the nearly collinear triples of nearby points the filter
+// leaves open cost a few TwoSums instead of a twelve-term expansion.
+QH_HD int diff_products_sign32(float a1, float a0, float b1, float b0, float c1, float c0, float d1, float d0,
+                               bool &decided) {
+    float x[4];
+    const float hi[4] = {a1, b1, c1, d1}, lo[4] = {a0, b0, c0, d0};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float e;
+        two_sum(hi[k], -lo[k], x[k], e);
+        ok = ok && e == 0.f && f32_exact_range(x[k]);
+    }
+    decided = ok;
+    if (!ok) return 0;
+    const float l = rmul(x[0], x[1]), r = rmul(x[2], x[3]);
+    float t[4] = {rfma(x[0], x[1], -l), -rfma(x[2], x[3], -r), l, -r};
+    return sum_sign_f32(t);
+}
+
 // orient(a,b,c) = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx, exactly.
 QH_HD_COLD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
     const float fa[6] = {bx, bx, ax, by, by, ay};
     const float fb[6] = {cy, ay, cy, cx, ax, cx};
     const int sg[6] = {1, -1, -1, -1, 1, 1};
+    bool decided;
     if (!factors_in_f32_range(fa, fb)) {
-        bool decided;
         const int s64 = diff_products_sign64(bx, ax, cy, ay, by, ay, cx, ax, decided);
         if (decided) return s64;
+    } else {
+        const int s32 = diff_products_sign32(bx, ax, cy, ay, by, ay, cx, ax, decided);
+        if (decided) return s32;
     }
     return product_sum_sign(fa, fb, sg);
 }
@@ -359,10 +386,13 @@ QH_HD_COLD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, 
     const float fa[8] = {vx, vx, ux, ux, vy, vy, uy, uy};
     const float fb[8] = {py, qy, py, qy, px, qx, px, qx};
     const int sg[8] = {-1, 1, 1, -1, 1, -1, -1, 1};
+    bool decided;  // the same value as (vy-uy)(px-qx) - (vx-ux)(py-qy)
     if (!factors_in_f32_range(fa, fb)) {
-        bool decided;  // the same value as (vy-uy)(px-qx) - (vx-ux)(py-qy)
         const int s64 = diff_products_sign64(vy, uy, px, qx, vx, ux, py, qy, decided);
         if (decided) return s64;
+    } else {
+        const int s32 = diff_products_sign32(vy, uy, px, qx, vx, ux, py, qy, decided);
+        if (decided) return s32;
     }
     return product_sum_sign(fa, fb, sg);
 }
