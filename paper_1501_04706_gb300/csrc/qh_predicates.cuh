@@ -113,6 +113,13 @@ QH_HD float add_up(float a, float b) {
     return std::nextafter(a + b, INFINITY);
 #endif
 }
+QH_HD float add_down(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rd(a, b);
+#else
+    return std::nextafter(a + b, -INFINITY);
+#endif
+}
 QH_HD double sub_down(double a, double b) {
 #ifdef __CUDA_ARCH__
     return __dsub_rd(a, b);
@@ -364,12 +371,59 @@ QH_HD int diff_products_sign32(float a1, float a0, float b1, float b0, float c1,
     return sum_sign_f32(t);
 }
 
+// The value (a1 - a0)(b1 - b0) - (c1 - c0)(d1 - d0) in compensated FP32 with a
+// certified bound, between the filter and the expansions.  Each difference is
+// split exactly by TwoSum into a high and a low part, so the value is exactly
+//   m1 + [m0 + p0 - q0 + ah bl + al bh - ch dl - cl dh + al bl - cl dl],
+// where p1 + p0 = ah bh and q1 + q0 = ch dh (FMA residues) and m1 + m0 =
+// p1 - q1 (TwoSum).  The bracket's nine terms are summed in round-to-nearest;
+// six of them are rounded products.  Its error is at most 8u (summation) + u
+// (products) times the sum of the magnitudes, plus 2^-150 for each product or
+// residue that underflows; 10u times the upward-rounded magnitude sum plus
+// 2^-144 bounds it (u = 2^-24).  The sign is decided when the directed-rounded
+// interval around m1 + bracket excludes zero; exact zeros and non-finite
+// intermediates stay undecided.
+QH_HD int diff_products_sign_comp(float a1, float a0, float b1, float b0, float c1, float c0, float d1, float d0,
+                                  bool &decided) {
+    float ah, al, bh, bl, ch, cl, dh, dl;
+    two_sum(a1, -a0, ah, al);
+    two_sum(b1, -b0, bh, bl);
+    two_sum(c1, -c0, ch, cl);
+    two_sum(d1, -d0, dh, dl);
+    const float p1 = rmul(ah, bh), p0 = rfma(ah, bh, -p1);
+    const float q1 = rmul(ch, dh), q0 = rfma(ch, dh, -q1);
+    float m1, m0;
+    two_sum(p1, -q1, m1, m0);
+    const float t[9] = {m0, p0, -q0, rmul(ah, bl), rmul(al, bh), -rmul(ch, dl), -rmul(cl, dh), rmul(al, bl),
+                        -rmul(cl, dl)};
+    float sum = 0.f, mag = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        sum = radd(sum, t[k]);
+        mag = add_up(mag, fabs_f(t[k]));
+    }
+    decided = false;
+    const float err = add_up(mul_up(mag, 10.f * 0x1p-24f), 0x1p-144f);
+    if (!(fabs_f(m1) <= FLT_MAX && fabs_f(sum) <= FLT_MAX && err <= FLT_MAX)) return 0;
+    if (sub_down(add_down(m1, sum), err) > 0.f) {
+        decided = true;
+        return 1;
+    }
+    if (add_up(add_up(m1, sum), err) < 0.f) {
+        decided = true;
+        return -1;
+    }
+    return 0;
+}
+
 // orient(a,b,c) = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx, exactly.
 QH_HD_COLD int orient_exact(float ax, float ay, float bx, float by, float cx, float cy) {
     const float fa[6] = {bx, bx, ax, by, by, ay};
     const float fb[6] = {cy, ay, cy, cx, ax, cx};
     const int sg[6] = {1, -1, -1, -1, 1, 1};
     bool decided;
+    const int sc = diff_products_sign_comp(bx, ax, cy, ay, by, ay, cx, ax, decided);
+    if (decided) return sc;
     if (!factors_in_f32_range(fa, fb)) {
         const int s64 = diff_products_sign64(bx, ax, cy, ay, by, ay, cx, ax, decided);
         if (decided) return s64;
@@ -387,6 +441,8 @@ QH_HD_COLD int dist_cmp_exact(float ux, float uy, float vx, float vy, float px, 
     const float fb[8] = {py, qy, py, qy, px, qx, px, qx};
     const int sg[8] = {-1, 1, 1, -1, 1, -1, -1, 1};
     bool decided;  // the same value as (vy-uy)(px-qx) - (vx-ux)(py-qy)
+    const int sc = diff_products_sign_comp(vy, uy, px, qx, vx, ux, py, qy, decided);
+    if (decided) return sc;
     if (!factors_in_f32_range(fa, fb)) {
         const int s64 = diff_products_sign64(vy, uy, px, qx, vx, ux, py, qy, decided);
         if (decided) return s64;
