@@ -1152,23 +1152,6 @@ __device__ __forceinline__ void pass1_commit(RoundSmem<P> &sm, unsigned cp0, uns
     }
 }
 
-// Reserve the tile's output range in each of nslot children; warp offsets.
-template <typename P> __device__ __forceinline__ void tile_reserve(RoundSmem<P> &sm, int nslot, int *const (&cursor)[4]) {
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        const int q = threadIdx.x;
-        int run = 0;
-        if (q < nslot) {
-            for (int w = 0; w < NWARP; w++) {
-                sm.warpOff[w][q] = run;
-                run += (int)sm.warpCnt[w][q];
-            }
-        }
-        sm.tot[q] = run;
-        sm.base[q] = run ? atomicAdd(cursor[q], run) : 0;
-    }
-    __syncthreads();
-}
 
 // Pass-2 rank of an item of slot c among its slot's points: the warp's running
 // rank plus the lane rank.
@@ -1247,14 +1230,33 @@ __device__ __noinline__ void resolve_tile_exhaustive(RoundSmem<P> &sm, int nslot
     }
 }
 
+// Threads q < 4 after the barrier that follows pass1_commit: the warp offsets
+// of slot q and the tile's reservation on the child's cursor.  The returned
+// base is used only after the candidate pass, so the atomic's round trip
+// overlaps it; the caller stores it to sm.base[q] before the next barrier.
+template <typename P> __device__ __forceinline__ int tile_reserve_issue(RoundSmem<P> &sm, int nslot,
+                                                                        int *const (&cursor)[4]) {
+    const int q = threadIdx.x;
+    int run = 0;
+    if (q < nslot) {
+        for (int w = 0; w < NWARP; w++) {
+            sm.warpOff[w][q] = run;
+            run += (int)sm.warpCnt[w][q];
+        }
+    }
+    sm.tot[q] = run;
+    return run ? atomicAdd(cursor[q], run) : 0;
+}
+
 // Exact best candidate per slot -> sm.best[q], written by thread q (q < nslot),
-// which may use it without a further barrier.  Usually a slot has one
-// candidate; overflowing lists (massive exact ties) fall back to a full exact
-// reduction over the tile.
+// which may use it without a further barrier.  The candidate lists are complete
+// (offered before a barrier the caller has passed), so there is no barrier
+// here: threads q < nslot resolve while the others write their survivors.
+// Usually a slot has one candidate; overflowing lists (massive exact ties) fall
+// back to a full exact reduction over the tile (the whole CTA).
 template <typename P, typename Fetch>
-__device__ __forceinline__ void resolve_candidates(RoundSmem<P> &sm, int nslot, int nItems, Fetch &&fetch,
-                                                   int &exact_c) {
-    __syncthreads();
+__device__ __forceinline__ void resolve_candidates_ready(RoundSmem<P> &sm, int nslot, int nItems, Fetch &&fetch,
+                                                         int &exact_c) {
     if (!sm.candOver) {
         if (threadIdx.x < nslot) {
             const int q = threadIdx.x, n = sm.nq[q];
@@ -1488,17 +1490,29 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
         pass1_commit(sm, cp0, cp1, pc, mlo);
         Inst *W = &p.inst[R.inst];
         int *const cursors[4] = {&W->chCount[0], &W->chCount[1], &W->chCount[2], &W->chCount[3]};
-        tile_reserve(sm, K, cursors);
-        // pass 2: write the survivors, then offer candidates
-        const long long off = R.setOff, n = R.setN;
         const int idBase = (int)(R.lt * q.ts);
-        int wr[4];
+        // reservation in flight while the farthest-point candidates are offered
+        __syncthreads();
         unsigned thr[4];
 #pragma unroll
-        for (int qq = 0; qq < 4; qq++) {
-            wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
-            thr[qq] = sm.maxLo[qq];
+        for (int qq = 0; qq < 4; qq++) thr[qq] = sm.maxLo[qq];
+        const int resv = threadIdx.x < 4 ? tile_reserve_issue(sm, K, cursors) : 0;
+        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
+            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
+                const int j = __ffs(m) - 1;
+                const int c = item_cls(j, cp0, cp1);
+                const int i = j * NT + threadIdx.x;
+                const float2 v = xs[i + dx];
+                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, idBase + i);
+            }
         }
+        if (threadIdx.x < 4) sm.base[threadIdx.x] = resv;
+        __syncthreads();
+        // pass 2: write the survivors (threads q < K then resolve slot q's candidates)
+        const long long off = R.setOff, n = R.setN;
+        int wr[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; qq++) wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
         float2 *oxy = p.xy[0];
         int *oid = p.id[0];
         bool bad = false;
@@ -1519,27 +1533,19 @@ __device__ __noinline__ bool phase_round0(const Params &p, unsigned long long &g
             }
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
-        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
-            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
-                const int j = __ffs(m) - 1;
-                const int c = item_cls(j, cp0, cp1);
-                const int i = j * NT + threadIdx.x;
-                const float2 v = xs[i + dx];
-                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, idBase + i);
-            }
-        }
         auto fetch = [&](int i, float &px, float &py, int &idx) {
             const float2 v = xs[i + dx];
             px = v.x;
             py = v.y;
             idx = idBase + i;
         };
-        resolve_candidates(sm, K, nItems, fetch, exact_c);
+        resolve_candidates_ready(sm, K, nItems, fetch, exact_c);
         if (threadIdx.x < K) imerge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
         if (threadIdx.x == 0) {
             sm.run.tiles++;
             survivors += (long long)sm.tot[0] + sm.tot[1] + sm.tot[2] + sm.tot[3];
         }
+        __syncthreads();  // every read of this tile's stage precedes its refill
         pipe_refill<P>(p, q, kt, s, gI);
     }
     __syncthreads();
@@ -1657,17 +1663,30 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
         Node *NA = &p.nodes[R.node[0]];
         Node *NB = &p.nodes[R.node[np == 2 ? 1 : 0]];
         int *const cursors[4] = {&NA->chCount[0], &NA->chCount[1], &NB->chCount[0], &NB->chCount[1]};
-        tile_reserve(sm, 2 * np, cursors);
-        // pass 2: write the survivors, then offer candidates
+        // reservation in flight while the farthest-point candidates are offered
+        __syncthreads();
+        unsigned thr[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; qq++) thr[qq] = sm.maxLo[qq];
+        const int resv = threadIdx.x < 4 ? tile_reserve_issue(sm, 2 * np, cursors) : 0;
+        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
+            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
+                const int j = __ffs(m) - 1;
+                const int c = item_cls(j, cp0, cp1);
+                const int i = j * NT + threadIdx.x;
+                const bool pb = (c == 2) | (c == 3);
+                const float2 v = xs[i + (pb ? dx1 : dx0)];
+                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, is[i + (pb ? di1 : di0)]);
+            }
+        }
+        if (threadIdx.x < 4) sm.base[threadIdx.x] = resv;
+        __syncthreads();
+        // pass 2: write the survivors (threads q < 2 np then resolve slot q's candidates)
         const long long ps0 = R.pstart[0], ps1 = R.pstart[1];
         const int cn0 = R.count[0], cn1 = R.count[1];
         int wr[4];
-        unsigned thr[4];
 #pragma unroll
-        for (int qq = 0; qq < 4; qq++) {
-            wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
-            thr[qq] = sm.maxLo[qq];
-        }
+        for (int qq = 0; qq < 4; qq++) wr[qq] = sm.base[qq] + sm.warpOff[w][qq];
         float2 *oxy = p.xy[dst];
         int *oid = p.id[dst];
         const long long lim = 2 * p.ncap;
@@ -1693,16 +1712,6 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             }
         }
         if (bad) set_err(p.ctl, E_INTERNAL);
-        if (const unsigned fl = candidate_slots(mhi, pc, thr)) {
-            for (unsigned m = items_in_slots(fl, cp0, cp1); m; m &= m - 1u) {
-                const int j = __ffs(m) - 1;
-                const int c = item_cls(j, cp0, cp1);
-                const int i = j * NT + threadIdx.x;
-                const bool pb = (c == 2) | (c == 3);
-                const float2 v = xs[i + (pb ? dx1 : dx0)];
-                offer_candidate(sm, c, sel4(c, thr), v.x, v.y, is[i + (pb ? di1 : di0)]);
-            }
-        }
         auto fetch = [&](int i, float &px, float &py, int &idx) {
             const bool pb = i >= vB;
             const float2 v = xs[i + (pb ? dx1 : dx0)];
@@ -1710,7 +1719,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             py = v.y;
             idx = is[i + (pb ? di1 : di0)];
         };
-        resolve_candidates(sm, 2 * np, nItems, fetch, exact_c);
+        resolve_candidates_ready(sm, 2 * np, nItems, fetch, exact_c);
         if (threadIdx.x < 2) imerge(sm.run.best[threadIdx.x], sm.best[threadIdx.x], threadIdx.x, sm, exact_c);
         if (threadIdx.x == 0) {
             sm.run.tiles++;
@@ -1726,6 +1735,7 @@ __device__ __noinline__ bool phase_round(const Params &p, unsigned long long &gI
             if (threadIdx.x < 2) sm.run.best[threadIdx.x] = sm.best[2 + threadIdx.x];
             if (threadIdx.x == 0) sm.run.tiles = 1;
         }
+        __syncthreads();  // every read of this tile's stage precedes its refill
         pipe_refill<P>(p, q, kt, s, gI);
     }
     __syncthreads();
