@@ -210,7 +210,6 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
         DistIv<P> dq = dist_interval(orient_approx(e, q.x, q.y));
         const P thr = (P)fkey_inv(s.maxLo[c]);
         if (!(dq.hi >= thr)) continue;
-        const int qi = fin_gidx(p, s, k);
         unsigned short cur = s.best[c];
         for (int it = 0; it < 1 << 20; it++) {
             bool mine;
@@ -218,9 +217,14 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
                 mine = true;
             } else {
                 const float2 w = s.pxy[cur];
-                const int wi = fin_gidx(p, s, cur);
-                DistIv<P> dw = dist_interval(orient_approx(e, w.x, w.y));
-                mine = farther(e, b.x, b.y, q.x, q.y, qi, dq, w.x, w.y, wi, dw, exact_c);
+                if (q.x == w.x && q.y == w.y) {
+                    // equal points: the original indices decide (a global load for
+                    // a segment's points, so only here)
+                    mine = fin_gidx(p, s, k) < fin_gidx(p, s, cur);
+                } else {  // the local indices only stand for "a point" here
+                    DistIv<P> dw = dist_interval(orient_approx(e, w.x, w.y));
+                    mine = farther(e, b.x, b.y, q.x, q.y, k, dq, w.x, w.y, (int)cur, dw, exact_c);
+                }
             }
             if (!mine) break;
             const unsigned short prev = atomicCAS(&s.best[c], cur, (unsigned short)k);
@@ -484,7 +488,9 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
     const int genLimit = gen + m + 4;  // every generation removes at least one point per live segment
     while (s.S > 0) {
         // one decision for the whole block: another block may set the error word meanwhile
-        if (__syncthreads_or(gen > genLimit || (threadIdx.x == 0 && ld_volatile(&p.ctl->err) != 0u))) {
+        // another block's error is polled every fourth generation (a global round trip)
+        if (__syncthreads_or(gen > genLimit ||
+                             (threadIdx.x == 0 && (gen & 3) == 0 && ld_volatile(&p.ctl->err) != 0u))) {
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             return;
         }
@@ -605,7 +611,9 @@ template <typename P> __device__ void fin_solve_pack(const Params &p, FinSmem &s
     const int genLimit = gen + m + 4;
     while (s.S > 0) {
         // one decision for the whole block: another block may set the error word meanwhile
-        if (__syncthreads_or(gen > genLimit || (threadIdx.x == 0 && ld_volatile(&p.ctl->err) != 0u))) {
+        // another block's error is polled every fourth generation (a global round trip)
+        if (__syncthreads_or(gen > genLimit ||
+                             (threadIdx.x == 0 && (gen & 3) == 0 && ld_volatile(&p.ctl->err) != 0u))) {
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             return;
         }
