@@ -121,9 +121,11 @@ __device__ __forceinline__ bool fin_right_of(const FinSmem &s, int u, int v, flo
 
 // One generation.  Classification (pass 1), exact farthest point per child
 // (pass 2), rebuild of the CCW head list and of the live segments, relabelling.
+// Returns (the same in the whole block) whether the generation failed or, when
+// pollErr is set, another block has reported an error.
 template <typename P>
-__device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial, OrdE *&ord, OrdE *&ordN,
-                               int gen, int &exact_o, int &exact_c) {
+__device__ bool fin_generation(const Params &p, FinSmem &s, int m, bool initial, OrdE *&ord, OrdE *&ordN,
+                               int gen, bool pollErr, int &exact_o, int &exact_c) {
     const int S = s.S, nOrd = s.nOrd;
     const int nch = initial ? s.K : 2 * S;
     for (int c = threadIdx.x; c < nch; c += FIN_NT) {
@@ -245,7 +247,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
             packed += (cnt > 0u ? 1 << 16 : 0) + (int)cnt;
         }
         int tot;
-        int x = block_excl_scan<int, FIN_NT>(packed, s.scan, tot) >> 16;
+        int x = block_excl_scan_open<int, FIN_NT>(packed, s.scan, tot) >> 16;  // a barrier follows
         for (int c = b; c < e; c++) {
             const unsigned cnt = initial ? s.cnt2[c] : ((s.cnt2[c >> 1] >> (16 * (c & 1))) & 0xffffu);
             s.newId[c] = cnt > 0u ? (unsigned short)(x++) : NONE16;
@@ -284,15 +286,14 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
             }
         }
         int tot;
-        const int x = block_excl_scan<int, FIN_NT>((w << 16) + __popc(km), s.scan, tot);
+        const int x = block_excl_scan_open<int, FIN_NT>((w << 16) + __popc(km), s.scan, tot);
         if (!initial && (tot >> 16) > ORDCAP - 8) {  // guard: at most one head per point plus the chord ends
             if (threadIdx.x == 0) {
                 set_err(p.ctl, E_INTERNAL);
                 s.S = 0;
                 s.nOrd = 0;
             }
-            __syncthreads();
-            return;
+            return __syncthreads_or(1);
         }
         int xl = x & 0xffff;
 #pragma unroll
@@ -339,7 +340,7 @@ __device__ void fin_generation(const Params &p, FinSmem &s, int m, bool initial,
     OrdE *t = ord;
     ord = ordN;
     ordN = t;
-    __syncthreads();
+    return __syncthreads_or(threadIdx.x == 0 && pollErr && ld_volatile(&p.ctl->err) != 0u);
 }
 
 template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, bool isNode, int id, int &exact_o,
@@ -482,19 +483,18 @@ template <typename P> __device__ void fin_solve(const Params &p, FinSmem &s, boo
             }
             return;
         }
-        fin_generation<P>(p, s, m, true, ord, ordN, 0, exact_o, exact_c);
+        fin_generation<P>(p, s, m, true, ord, ordN, 0, false, exact_o, exact_c);
         gen = 1;
     }
     const int genLimit = gen + m + 4;  // every generation removes at least one point per live segment
+    bool stop = false;
     while (s.S > 0) {
-        // one decision for the whole block: another block may set the error word meanwhile
-        // another block's error is polled every fourth generation (a global round trip)
-        if (__syncthreads_or(gen > genLimit ||
-                             (threadIdx.x == 0 && (gen & 3) == 0 && ld_volatile(&p.ctl->err) != 0u))) {
+        if (stop || gen > genLimit) {  // the same in the whole block
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             return;
         }
-        fin_generation<P>(p, s, m, false, ord, ordN, gen, exact_o, exact_c);
+        // another block's error is polled every fourth generation (a global round trip)
+        stop = fin_generation<P>(p, s, m, false, ord, ordN, gen, (gen & 3) == 0, exact_o, exact_c);
         gen++;
     }
     const int nOrd = s.nOrd;
@@ -609,15 +609,14 @@ template <typename P> __device__ void fin_solve_pack(const Params &p, FinSmem &s
     }
     int gen = level + 1;
     const int genLimit = gen + m + 4;
+    bool stop = false;
     while (s.S > 0) {
-        // one decision for the whole block: another block may set the error word meanwhile
-        // another block's error is polled every fourth generation (a global round trip)
-        if (__syncthreads_or(gen > genLimit ||
-                             (threadIdx.x == 0 && (gen & 3) == 0 && ld_volatile(&p.ctl->err) != 0u))) {
+        if (stop || gen > genLimit) {  // the same in the whole block
             if (threadIdx.x == 0) set_err(p.ctl, E_INTERNAL);
             return;
         }
-        fin_generation<P>(p, s, m, false, ord, ordN, gen, exact_o, exact_c);
+        // another block's error is polled every fourth generation (a global round trip)
+        stop = fin_generation<P>(p, s, m, false, ord, ordN, gen, (gen & 3) == 0, exact_o, exact_c);
         gen++;
     }
     const int nOrd = s.nOrd;

@@ -366,6 +366,26 @@ __device__ __forceinline__ T block_excl_scan(T v, T *scratch, T &total) {
     return r;
 }
 
+// The same without the closing barrier, for callers that pass a CTA barrier
+// before the scratch is written again.
+template <typename T, int NTHREADS>
+__device__ __forceinline__ T block_excl_scan_open(T v, T *scratch, T &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = NTHREADS / 32;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) scratch[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < NW ? scratch[lane] : T(0);
+        T si = warp_incl_scan(s);
+        if (lane < NW) scratch[lane] = si - s;
+        if (lane == NW - 1) scratch[NW] = si;
+    }
+    __syncthreads();
+    total = scratch[NW];
+    return scratch[w] + inc - v;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
