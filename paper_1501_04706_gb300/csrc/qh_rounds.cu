@@ -1008,9 +1008,10 @@ __device__ __noinline__ void ext_flush(const Params &p, Ext e, int i, long long 
 // (4 bits per item), counts the points of every slot per thread (8-bit
 // fields) and keeps, per slot, the largest lower distance bound.  One
 // reservation per (tile, slot) on the child's cursor then gives every warp its
-// output range, and pass 2 writes the survivors (ranks from warp ballots, so
-// stores are coalesced) and collects the candidates whose upper bound reaches
-// the slot's largest lower bound.
+// output range; while its round trip is in flight the items whose upper bound
+// reaches their slot's largest lower bound are offered as farthest-point
+// candidates.  Pass 2 writes the survivors (ranks from warp ballots, so stores
+// are coalesced) while one thread per slot resolves the slot's candidates.
 
 // Record the slot c (CLS_NONE: discarded) of item j with the keys of its
 // distance bounds.
