@@ -110,13 +110,14 @@ qh_status qh_plan_set_flags(qh_plan plan, uint32_t flags);
  * kernel variant (32 x points per thread, so a tile never spans more than two
  * segments) to 4096.  timing: 1 records CUDA events between the kernels so
  * qh_plan_get_stats can report per-phase times.  grid_ctas_per_sm: 0 =
- * occupancy maximum.
+ * automatic (one CTA per SM for a single set of at most 2^19 points, else the
+ * occupancy maximum).
  */
 qh_status qh_plan_set_tuning(qh_plan plan, int32_t cutover, int32_t timing, int32_t grid_ctas_per_sm);
 
 /*
  * Kernel variant of the grid-wide rounds: threads per block (256 or 128) and points per thread per tile (16
- * or 8; a tile is one warp's unit of work, 32 x points per thread).  Each call keeps the other knob, raises
+ * or 8; a tile is threads x points per thread points).  Each call keeps the other knob, raises
  * the cutover to the new tile if needed and resets grid_ctas_per_sm to the occupancy maximum.  Other values:
  * QH_ERR_INVALID_ARG.  (Not in the paper: its kernels are Thrust calls with library-chosen launch shapes.)
  */
@@ -132,7 +133,8 @@ qh_status qh_plan_set_items_per_thread(qh_plan plan, int32_t items_per_thread);
  */
 qh_status qh_plan_set_debug(qh_plan plan, uint32_t spin_limit, int32_t max_tree_nodes);
 
-/* The plan's current tuning: block size, points per thread, small-segment cutover, grid CTAs per SM. */
+/* The plan's current tuning: block size, points per thread, small-segment cutover, grid CTAs per SM (when
+ * automatic: the occupancy maximum, which single sets of at most 2^19 points do not use). */
 qh_status qh_plan_get_tuning(qh_plan plan, int32_t *threads_per_block, int32_t *items_per_thread,
                              int32_t *cutover, int32_t *grid_ctas_per_sm);
 
