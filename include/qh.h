@@ -3,7 +3,7 @@
  *
  * Method: Zhang, Mei, Xu, Zhao, "A Novel Implementation of QuickHull Algorithm
  * on the GPU".  The library computes the convex hull of planar FP32 point sets
- * (Sec. 1: "the convex polygon that encloses all the points") with the
+ * (Sec. 1: the smallest convex polygon containing every point) with the
  * segmented, generation-synchronous QuickHull of Sec. 3-4: extreme points and an
  * initial split (Sec. 4.2-4.3), then rounds of farthest point per segment
  * (Sec. 4.4.1), segment update (Sec. 4.4.2, 4.4.4) and discard of interior
