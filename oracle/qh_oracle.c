@@ -14,10 +14,10 @@
  *
  * Two independent routes to that result:
  *
- *  qho_hull2d     Andrew's monotone chain (the "Monotone chain" of Sec. 1 and
- *                 Sec. 3): sort by (x, y, index), drop coordinate duplicates,
- *                 build the lower and upper chains popping while the turn is
- *                 not strictly counter-clockwise.
+ *  qho_hull2d     Andrew's monotone chain (named in Sec. 1 and Sec. 3): sort
+ *                 by (x, y, index), drop coordinate duplicates, build the
+ *                 lower and upper chains popping while the turn is not
+ *                 strictly counter-clockwise.
  *
  *  qho_quickhull  the generation-synchronous QuickHull rounds of Sec. 3-4.4:
  *                 initial split (chord A->B, or the quadrilateral of the four
