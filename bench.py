@@ -169,10 +169,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU-baseline legs")
-    ap.add_argument("--study", choices=["modes", "sweep", "profile", "configs"], default=None,
+    ap.add_argument("--study", choices=["modes", "sweep", "profile", "configs", "sorted"], default=None,
                     help="instead of the benchmark line: the five workloads in their stated forms (configs), "
                          "quadrilateral vs chord initial split (modes), "
-                         "uniform-square size sweep (sweep) or per-sub-procedure times (profile), one JSON line each")
+                         "uniform-square size sweep (sweep), per-sub-procedure times (profile) or the x-sorted "
+                         "form of the rounds against the unsorted one (sorted), one JSON line each")
+    ap.add_argument("--cases", default=None,
+                    help="sorted study: comma-separated workloads (disk-20M, circle-20M, degenerate-16M, "
+                         "square-100K, square-2M, square-20M; default all)")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the disk workload (default: the 20M-point benchmark; smaller sizes for profiling)")
     args = ap.parse_args()
@@ -181,7 +185,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.study:
-        return run_study(args.study)
+        return run_study(args.study, args.cases)
 
     import numpy as np
     import torch
@@ -443,14 +447,17 @@ def _time_hull(qh, torch, d_pts, plan, flush, reps: int = 5):
     return times[len(times) // 2], plan.stats(), int(cnt.item())
 
 
-def run_study(study: str) -> None:
+def run_study(study: str, cases: str | None = None) -> None:
     """Studies beside the benchmark (one JSON line per case):
     modes   -- the quadrilateral initial split (the paper's Mode 1) against the chord split (Mode 2) on the
                single-set workloads: device time and live points per generation;
     sweep   -- uniform unit square from 100K to 20M points in both modes, with the paper's K20c times (Table 2)
                as context;
     profile -- the time of each sub-procedure (set prep, extreme points, initial split, every grid round,
-               block finisher, output) on every workload, from the device clock and CUDA events."""
+               block finisher, output) on every workload, from the device clock and CUDA events;
+    sorted  -- the x-sorted form of the rounds (qh_hull2d_sorted, the paper's arrangement) against the
+               unsorted plan path on the same input: device times, its phases, identical hulls, and the
+               algorithmic bytes of both."""
     import numpy as np
     import torch
 
@@ -467,6 +474,8 @@ def run_study(study: str) -> None:
     modes = [("quadrilateral", qh.MODE_QUAD), ("chord", qh.MODE_CHORD)]
     if study == "configs":
         return _study_configs(qh, torch, np, synth, device, flush)
+    if study == "sorted":
+        return _study_sorted(qh, torch, np, synth, device, flush, cases)
     if study in ("modes", "profile"):
         cases = [("square-100K", synth.square()), ("disk-20M", synth.disk()), ("circle-20M", synth.circle()),
                  ("degenerate-16M", synth.degenerate())]
@@ -522,6 +531,78 @@ def _alg_bytes(n: int, live, h: int) -> int:
     for r in range(1, len(live)):
         b += 12 * (live[r - 1] + live[r])
     return b
+
+
+def _alg_bytes_sorted(n: int, live, items: int, h: int) -> dict:
+    """Algorithmic bytes of the x-sorted form by step: extreme points 8n; first split 8n read and 8 B
+    written per item (x key, payload); radix sort 4 passes of 20 B per item (4 read by the histogram,
+    8 read and 8 written by the scatter); gather 4 B payload, 8 B coordinates and 12 B written per item;
+    round r: 8 + 8 + 12 B read per point of generation r - 1 (farthest point, count, move) and 12 B written
+    per point of generation r; output 8h.  Heads (at most h per round) are not counted."""
+    live = [int(v) for v in live]
+    rounds = sum(28 * live[r - 1] + 12 * live[r] for r in range(1, len(live)))
+    if len(live) > 0:
+        rounds += 28 * live[-1]  # the last round reads its generation and keeps no point
+    b = {"extreme_points": 8 * n, "first_split": 8 * n + 8 * items, "sort": 80 * items, "gather": 24 * items,
+         "rounds": rounds, "output": 8 * h}
+    b["total"] = sum(b.values())
+    return b
+
+
+def _study_sorted(qh, torch, np, synth, device, flush, cases):
+    """The x-sorted form against the unsorted plan path, both initial splits, same plan and input."""
+    all_cases = [("disk-20M", synth.disk), ("circle-20M", synth.circle), ("degenerate-16M", synth.degenerate),
+                 ("square-100K", lambda: synth.square(100_000)), ("square-2M", lambda: synth.square(2_000_000)),
+                 ("square-20M", lambda: synth.square(20_000_000))]
+    want = set(cases.split(",")) if cases else None
+    for name, gen in all_cases:
+        if want is not None and name not in want:
+            continue
+        pts = gen()
+        n = len(pts)
+        d_pts = torch.from_numpy(pts).to(device)
+        out = torch.empty(n, dtype=torch.int32, device=device)
+        cnt = torch.empty(1, dtype=torch.int32, device=device)
+        plan = qh.Plan(n, 1)
+        for mname, mode in (("quadrilateral", qh.MODE_QUAD), ("chord", qh.MODE_CHORD)):
+            plan.set_flags(mode, qh.PREC_F32)
+            ms_u, st_u, h = _time_hull(qh, torch, d_pts, plan, flush)
+            ref = qh.hull2d(d_pts, plan).cpu().numpy()
+            got = qh.hull2d_sorted(d_pts, plan, out, cnt).cpu().numpy()
+            times = []
+            for _ in range(5):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                qh.hull2d_sorted(d_pts, plan, out, cnt)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            times.sort()
+            ms_s = times[len(times) // 2]
+            plan.set_tuning(4096, timing=True)
+            flush.fill_(1)
+            qh.hull2d_sorted(d_pts, plan, out, cnt)
+            st_s = plan.stats()
+            plan.set_tuning(4096, timing=False)
+            live = [int(v) for v in st_s["live"]]
+            items = live[0] + (2 if mname == "chord" else 4)  # survivors of the first split and the polygon
+            ph = st_s["phase_ms"]
+            print(json.dumps({
+                "study": "sorted", "workload": name, "mode": mname, "n": n, "hull_vertices": h,
+                "ms_unsorted": ms_u, "ms_sorted": ms_s, "sorted_over_unsorted": ms_s / ms_u,
+                "same_hull": bool(np.array_equal(got, ref)), "same_live_counts": st_s["live"] == st_u["live"],
+                "generations": st_s["generations"],
+                "sorted_phases_ms": {"extreme_points_and_first_split": ph[0], "sort_and_gather": ph[1],
+                                     "rounds": ph[2], "output": ph[3], "total": ph[4]},
+                "algorithmic_gb": {"unsorted": _alg_bytes(n, st_u["live"], h) / 1e9,
+                                   "sorted": {k: v / 1e9 for k, v in _alg_bytes_sorted(n, live, items, h).items()}},
+                "round_bytes_per_point": {"unsorted": {"read": 12, "written": 12},
+                                          "sorted": {"read": 28, "written": 12}},
+                "note": "sorted form: one host check of the end flag per 8 rounds, inside the timed region"}),
+                flush=True)
+        plan.close()
+        del d_pts
 
 
 def _study_configs(qh, torch, np, synth, device, flush):

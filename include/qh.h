@@ -192,6 +192,28 @@ qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *of
                             int32_t *out_idx, int32_t *out_counts, qh_stream_t stream);
 
 /*
+ * qh_hull2d_sorted -- the hull of one set by the paper's own arrangement of the
+ * rounds (Sec. 3, Sec. 4.2-4.4): after the first split the points are sorted by
+ * x (the lower subset ascending, the upper one descending), so that all of them
+ * read as one polygon from the lexicographic minimum; every round marks the
+ * farthest point of each segment as a head in place and a stable compaction
+ * removes the points that are not strictly right of their new chord.  The
+ * result equals qh_hull2d_p's (same vertices, same order, same per-generation
+ * live counts in the statistics) for the plan's mode and precision flags.
+ *   points, n, out_idx, out_count, stream: as for qh_hull2d_p.
+ * Scratch: the first call allocates about 60 bytes per point of the plan's
+ * capacity in the plan (kept until qh_plan_destroy).  The host reads an end
+ * flag after every 8 rounds, so the call synchronizes the stream and returns
+ * once the hull is written; it cannot be captured in a CUDA graph
+ * (QH_ERR_UNSUPPORTED while the stream is capturing).  With timing on, the
+ * statistics' phase_ms hold: first split (with the extreme points), sort,
+ * rounds (including the host's checks), output, total.
+ * Errors: as qh_hull2d_p; QH_ERR_INTERNAL when the device state is inconsistent.
+ */
+qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                           qh_stream_t stream);
+
+/*
  * qh_hull2d_host -- end-to-end form of qh_hull2d_p with HOST buffers: copies
  * host_points (float[2*n]) to the device, computes, copies the hull to
  * host_out_idx (int32[n]) and the count to *host_out_count, and synchronizes

@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
     lib.qh_hull2d.argtypes = [vp, i64, vp, vp, vp]
     lib.qh_hull2d_batched.argtypes = [vp, vp, vp, i32, vp, vp, vp]
     lib.qh_hull2d_host.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.qh_hull2d_sorted.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.qh_plan_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.qh_status_string.argtypes = [ctypes.c_int]
     lib.qh_status_string.restype = ctypes.c_char_p
@@ -88,7 +89,8 @@ def load() -> ctypes.CDLL:
     for f in ("qh_plan_create", "qh_plan_destroy", "qh_plan_set_flags", "qh_plan_set_tuning", "qh_plan_set_block",
               "qh_plan_set_debug", "qh_hull2d_noalloc", "qh_plan_set_items_per_thread",
               "qh_plan_get_tuning", "qh_plan_autotune", "qh_hull2d_p",
-              "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_plan_get_stats", "qh_check_orient_host",
+              "qh_hull2d", "qh_hull2d_batched", "qh_hull2d_host", "qh_hull2d_sorted", "qh_plan_get_stats",
+              "qh_check_orient_host",
               "qh_check_orient_device", "qh_check_dist_host", "qh_check_dist_device"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -325,6 +327,30 @@ def hull2d_batched(points, offsets, plan: Plan, out=None, counts=None):
     _check(lib.qh_hull2d_batched(plan.handle, pts.data_ptr(), off.data_ptr(), num_sets, out.data_ptr(),
                                  counts.data_ptr(), _stream(pts.device)), "qh_hull2d_batched")
     return out, counts[:num_sets]
+
+
+def hull2d_sorted(points, plan: Plan, out=None, count=None):
+    """Hull of one point set by the x-sorted form of the rounds (qh_hull2d_sorted).
+
+    Same result as ``hull2d`` for the plan's flags; the call synchronizes the stream.
+    Returns the int32 index tensor.
+    """
+    import torch
+
+    lib = load()
+    pts = _points_tensor(points)
+    n = pts.shape[0]
+    dev = pts.device
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib.qh_hull2d_sorted(plan.handle, pts.data_ptr(), n, out.data_ptr(), count.data_ptr(), _stream(dev)),
+           "qh_hull2d_sorted")
+    c = int(count.item())
+    if c < 0:
+        raise QhError(-c, "qh_hull2d_sorted (device)")
+    return out[:c]
 
 
 def hull2d_host(points: np.ndarray, plan: Plan, out: np.ndarray | None = None) -> np.ndarray:

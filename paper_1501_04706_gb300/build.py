@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libqh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu", "qh_noalloc.cu"]
+SOURCES = ["qh_rounds.cu", "qh_finish.cu", "qh_api.cu", "qh_noalloc.cu", "qh_sorted.cu"]
 # Translation units: (source, object name, flags).  The grid-wide kernel is compiled once per variant
 # (threads per CTA, points per thread, CTAs per SM it is built for), each in its own namespace; the plan
 # picks one at run time.
@@ -27,8 +27,9 @@ UNITS = [("qh_rounds.cu", "qh_rounds_v256", ["-DQH_NT=256", "-DQH_IPT=16", "-DQH
          ("qh_rounds.cu", "qh_rounds_v128i8", ["-DQH_NT=128", "-DQH_IPT=8", "-DQH_MINB=6", "-DQH_VARIANT_NS=v128i8"]),
          ("qh_finish.cu", "qh_finish", []),
          ("qh_api.cu", "qh_api", []),
-         ("qh_noalloc.cu", "qh_noalloc", [])]
-HEADERS = ["qh_internal.cuh", "qh_predicates.cuh"]
+         ("qh_noalloc.cu", "qh_noalloc", []),
+         ("qh_sorted.cu", "qh_sorted", [])]
+HEADERS = ["qh_internal.cuh", "qh_predicates.cuh", "qh_sorted.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",

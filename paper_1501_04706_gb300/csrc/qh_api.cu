@@ -9,6 +9,7 @@
 
 #include "../../include/qh.h"
 #include "qh_internal.cuh"
+#include "qh_sorted.cuh"
 
 using namespace qh;
 
@@ -60,6 +61,8 @@ struct qh_plan_s {
     int *stOut = nullptr;
     int *stCnt = nullptr;
     long long stCap = 0;
+    // scratch of the x-sorted form, allocated by its first call
+    sx::SortedWs *sorted = nullptr;
 };
 
 namespace {
@@ -102,6 +105,10 @@ void plan_free(qh_plan p) {
     cudaFree(p->stIn);
     cudaFree(p->stOut);
     cudaFree(p->stCnt);
+    if (p->sorted) {
+        sx::sorted_free(*p->sorted);
+        delete p->sorted;
+    }
     if (p->hctl) cudaFreeHost(p->hctl);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
@@ -521,6 +528,46 @@ qh_status qh_hull2d_batched(qh_plan plan, const float *points, const int64_t *of
     if (num_sets == 0) return QH_OK;
     return run(plan, points, reinterpret_cast<const long long *>(offsets), 0, num_sets, out_idx, out_counts,
                (cudaStream_t)stream);
+}
+
+qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                           qh_stream_t stream) {
+    if (!plan || n < 0 || !out_count || (n > 0 && (!points || !out_idx))) return QH_ERR_INVALID_ARG;
+    if (((uintptr_t)points & 7u) != 0) return QH_ERR_INVALID_ARG;
+    if (n > plan->ncap) return QH_ERR_CAPACITY;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) return QH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (cs != cudaStreamCaptureStatusNone) return QH_ERR_UNSUPPORTED;  // the host reads the end flag
+    if (!plan->sorted) {
+        sx::SortedWs *w = new (std::nothrow) sx::SortedWs();
+        if (!w) return QH_ERR_OOM;
+        e = sx::sorted_alloc(*w, plan->ncap);
+        if (e != cudaSuccess) {
+            sx::sorted_free(*w);
+            delete w;
+            return cuda_status(e);
+        }
+        plan->sorted = w;
+    }
+    plan->last = s;
+    plan->lastSets = 1;
+    plan->evRecorded = false;
+    if (n == 0) {
+        e = cudaMemsetAsync(plan->ctl, 0, sizeof(Ctl), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(out_count, 0, sizeof(int32_t), s);
+        return cuda_status(e);
+    }
+    const bool tm = plan->timing != 0;
+    const int st = sx::sorted_run(*plan->sorted, reinterpret_cast<const float2 *>(points), (int)n,
+                                  (plan->flags & QH_MODE_CHORD) ? 1 : 0, (plan->flags & QH_PREC_F64) ? 1 : 0, out_idx,
+                                  out_count, plan->ctl, plan->numSMs, s, tm ? plan->ev : nullptr);
+    plan->evRecorded = tm && st == QH_OK;
+    return (qh_status)st;
 }
 
 qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
