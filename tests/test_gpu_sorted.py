@@ -155,6 +155,38 @@ def test_same_as_plan_path_on_reuse(qh, plans):
         assert np.array_equal(_sorted(qh, plan, p[: 1 + seed * 1000]), oracle.hull2d(p[: 1 + seed * 1000]))
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")  # the refused call leaves the capture empty
+def test_errors(qh):
+    """Argument errors return before any device work; a capturing stream is refused (the host reads the
+    end flag between batches of rounds); the plan works normally afterwards."""
+    import ctypes
+
+    import torch
+
+    lib = qh.load()
+    plan = qh.Plan(1000, 1)
+    p = synth.disk(2000, seed=3)
+    with pytest.raises(qh.QhError) as e:
+        _sorted(qh, plan, p)
+    assert e.value.status == 5  # QH_ERR_CAPACITY: more points than the plan holds
+    t = _dev(p[:1000])
+    out = torch.empty(1000, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.qh_hull2d_sorted(plan.handle, t.data_ptr() + 4, 999, out.data_ptr(), cnt.data_ptr(), s) == 1
+    assert lib.qh_hull2d_sorted(plan.handle, t.data_ptr(), -1, out.data_ptr(), cnt.data_ptr(), s) == 1
+    assert lib.qh_hull2d_sorted(plan.handle, t.data_ptr(), 10, out.data_ptr(), None, s) == 1
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    status = []
+    with torch.cuda.graph(graph, stream=stream):
+        status.append(lib.qh_hull2d_sorted(plan.handle, t.data_ptr(), 1000, out.data_ptr(), cnt.data_ptr(),
+                                           stream.cuda_stream))
+    assert status == [8]  # QH_ERR_UNSUPPORTED while capturing
+    assert np.array_equal(_sorted(qh, plan, p[:1000]), oracle.hull2d(p[:1000]))
+    plan.close()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["disk", "circle"])
 def test_full_size(qh, name):
