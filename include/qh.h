@@ -220,6 +220,14 @@ qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t
  * the stream before returning.  Entries of host_out_idx past the count are
  * unspecified (the first min(n, 65536) entries are read back together with the
  * count).  Pinned host memory gives the fastest copies.
+ * Sets of at least 2^22 points overlap the copy with the computation: the
+ * second half is copied on a side stream of the plan while the first half is
+ * hulled, then the first half's hull vertices are hulled together with the
+ * second half (the same output).  The plan's statistics then describe that
+ * second hull.  Scratch: staging for the copies (about 12 bytes
+ * per point) and, for the overlapped form, about 16 more, kept in the plan.
+ * Errors: as qh_hull2d_p, QH_ERR_INVALID_ARG when the current device is not the
+ * plan's.
  */
 qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
                          int32_t *host_out_count, qh_stream_t stream);

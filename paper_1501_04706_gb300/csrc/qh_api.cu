@@ -59,8 +59,15 @@ struct qh_plan_s {
     // end-to-end staging
     float *stIn = nullptr;
     int *stOut = nullptr;
-    int *stCnt = nullptr;
+    int *stCnt = nullptr;     // 8 counters (see qh_hull2d_host)
     long long stCap = 0;
+    // overlapped host path: side copy stream, its events, and the merge of the two halves' hulls
+    cudaStream_t cpStream = nullptr;
+    cudaEvent_t cpEv[2] = {nullptr, nullptr};
+    float2 *mPts = nullptr;     // vertices of the first half's hull
+    int *mOut = nullptr;        // hull of those vertices and the second half (local indices)
+    int *fOut = nullptr;        // final indices
+    long long *mOff = nullptr;  // that set's range in the staging buffer
     // scratch of the x-sorted form, allocated by its first call
     sx::SortedWs *sorted = nullptr;
 };
@@ -105,6 +112,13 @@ void plan_free(qh_plan p) {
     cudaFree(p->stIn);
     cudaFree(p->stOut);
     cudaFree(p->stCnt);
+    cudaFree(p->mPts);
+    cudaFree(p->mOut);
+    cudaFree(p->fOut);
+    cudaFree(p->mOff);
+    for (auto &e : p->cpEv)
+        if (e) cudaEventDestroy(e);
+    if (p->cpStream) cudaStreamDestroy(p->cpStream);
     if (p->sorted) {
         sx::sorted_free(*p->sorted);
         delete p->sorted;
@@ -253,6 +267,57 @@ qh_status run(qh_plan pl, const float *points, const long long *offsets, long lo
     pl->last = s;
     pl->lastSets = numSets;
     return QH_OK;
+}
+
+// The overlapped host path hulls the first half of a large set while the
+// second half is still being copied, then hulls the first half's vertices
+// together with the second half: every vertex of the whole hull is a vertex of
+// the first half's hull or a point of the second half.  The first half's
+// vertices are placed right before the second half, so their indices (all
+// below the second half's) come first and coordinate duplicates still resolve
+// to the lowest input index.
+__global__ void merge_gather_kernel(const float2 *pts, long long n1, long long n, const int *hull1, const int *c1p,
+                                    float2 *mPts, long long *mOff, int *mSt) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c1 = *c1p;
+    if (c1 < 0) {
+        if (gt == 0) {
+            mOff[0] = 0;
+            mOff[1] = 0;
+            *mSt = c1;
+        }
+        return;
+    }
+    for (long long k = gt; k < c1; k += (long long)gridDim.x * blockDim.x) mPts[k] = pts[hull1[k]];
+    if (gt == 0) {
+        mOff[0] = n1 - c1;
+        mOff[1] = n;
+        *mSt = 0;
+    }
+}
+
+// The gathered vertices into the places right before the second half (a
+// separate launch: the gather reads the first half where this one writes).
+__global__ void merge_place_kernel(float2 *pts, long long n1, const int *c1p, const float2 *mPts) {
+    const int c1 = *c1p;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < c1; k += (long long)gridDim.x * blockDim.x)
+        pts[n1 - c1 + k] = mPts[k];
+}
+
+__global__ void merge_map_kernel(long long n1, const int *hull1, const int *c1p, const int *mOut, const int *mCnt,
+                                 const int *mSt, int *out, int *count) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int st = *mSt, h = *mCnt, c1 = *c1p;
+    if (st < 0 || h < 0) {
+        if (gt == 0) *count = st < 0 ? st : h;
+        return;
+    }
+    const int *res = mOut + (n1 - c1);  // the merged set's output starts at its offset
+    for (long long k = gt; k < h; k += (long long)gridDim.x * blockDim.x) {
+        const int j = res[k];
+        out[k] = j < c1 ? hull1[j] : (int)(n1 + (j - c1));
+    }
+    if (gt == 0) *count = h;
 }
 
 struct DefaultPlans {
@@ -570,42 +635,110 @@ qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t
     return (qh_status)st;
 }
 
+namespace {
+// Sets of at least this many points take the overlapped host path: the copy of
+// the second half runs on a side stream while the first half is hulled.
+constexpr long long HOST_SPLIT_MIN = 1ll << 22;
+
+qh_status host_staging(qh_plan plan, long long n, bool split, cudaStream_t s) {
+    if (plan->stCap >= n && plan->stIn && (!split || plan->mPts)) return QH_OK;
+    cudaStreamSynchronize(s);
+    cudaFree(plan->stIn);
+    cudaFree(plan->stOut);
+    cudaFree(plan->stCnt);
+    cudaFree(plan->mPts);
+    cudaFree(plan->mOut);
+    cudaFree(plan->fOut);
+    cudaFree(plan->mOff);
+    plan->stIn = nullptr;
+    plan->stOut = nullptr;
+    plan->stCnt = nullptr;
+    plan->mPts = nullptr;
+    plan->mOut = nullptr;
+    plan->fOut = nullptr;
+    plan->mOff = nullptr;
+    plan->stCap = 0;
+    const long long cap = n < 1024 ? 1024 : n;
+    cudaError_t e = cudaMalloc((void **)&plan->stIn, sizeof(float) * 2 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stOut, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stCnt, sizeof(int) * 8);
+    if (e == cudaSuccess && split) e = cudaMalloc((void **)&plan->mPts, sizeof(float2) * (size_t)cap);
+    if (e == cudaSuccess && split) e = cudaMalloc((void **)&plan->mOut, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess && split) e = cudaMalloc((void **)&plan->fOut, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess && split) e = cudaMalloc((void **)&plan->mOff, sizeof(long long) * 2);
+    if (e == cudaSuccess && split && !plan->cpStream) e = cudaStreamCreateWithFlags(&plan->cpStream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess && split; k++)
+        if (!plan->cpEv[k]) e = cudaEventCreateWithFlags(&plan->cpEv[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+    plan->stCap = cap;
+    return QH_OK;
+}
+
+// Enqueue the overlapped host path; the result goes to plan->fOut and plan->stCnt[4].
+qh_status host_split_hull(qh_plan plan, const float *host_points, long long n, cudaStream_t s) {
+    const long long n1 = n / 2, n2 = n - n1;
+    int *cnt = plan->stCnt;  // [0]: the first half's hull; [2]: the merged set's; [3]: merge status; [4]: final
+    float2 *pts = reinterpret_cast<float2 *>(plan->stIn);
+    cudaError_t e = cudaEventRecord(plan->cpEv[0], s);  // the buffers' earlier users on s are done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->cpStream, plan->cpEv[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pts, host_points, sizeof(float2) * (size_t)n1, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pts + n1, host_points + 2 * n1, sizeof(float2) * (size_t)n2, cudaMemcpyHostToDevice,
+                            plan->cpStream);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->cpEv[1], plan->cpStream);
+    if (e != cudaSuccess) return cuda_status(e);
+    qh_status st = qh_hull2d_p(plan, plan->stIn, n1, plan->stOut, cnt, (qh_stream_t)s);
+    if (st != QH_OK) return st;
+    const int g = plan->numSMs * 4;
+    merge_gather_kernel<<<g, 256, 0, s>>>(pts, n1, n, plan->stOut, cnt, plan->mPts, plan->mOff, cnt + 3);
+    merge_place_kernel<<<g, 256, 0, s>>>(pts, n1, cnt, plan->mPts);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->cpEv[1], 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = qh_hull2d_batched(plan, plan->stIn, reinterpret_cast<const int64_t *>(plan->mOff), 1, plan->mOut, cnt + 2,
+                           (qh_stream_t)s);
+    if (st != QH_OK) return st;
+    merge_map_kernel<<<g, 256, 0, s>>>(n1, plan->stOut, cnt, plan->mOut, cnt + 2, cnt + 3, plan->fOut, cnt + 4);
+    return cuda_status(cudaGetLastError());
+}
+}  // namespace
+
 qh_status qh_hull2d_host(qh_plan plan, const float *host_points, int64_t n, int32_t *host_out_idx,
                          int32_t *host_out_count, qh_stream_t stream) {
     if (!plan || n < 0 || !host_out_count || (n > 0 && (!host_points || !host_out_idx))) return QH_ERR_INVALID_ARG;
     if (n > plan->ncap) return QH_ERR_CAPACITY;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) return QH_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (plan->stCap < n || !plan->stIn) {
-        cudaStreamSynchronize(s);
-        cudaFree(plan->stIn);
-        cudaFree(plan->stOut);
-        cudaFree(plan->stCnt);
-        plan->stIn = nullptr;
-        plan->stOut = nullptr;
-        plan->stCnt = nullptr;
-        long long cap = n < 1024 ? 1024 : n;
-        cudaError_t e = cudaMalloc((void **)&plan->stIn, sizeof(float) * 2 * (size_t)cap);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stOut, sizeof(int) * (size_t)cap);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&plan->stCnt, sizeof(int));
+    const bool split = n >= HOST_SPLIT_MIN;
+    qh_status st = host_staging(plan, n, split, s);
+    if (st != QH_OK) return st;
+    const int *resIdx = plan->stOut, *resCnt = plan->stCnt;
+    cudaError_t e = cudaSuccess;
+    if (split) {
+        st = host_split_hull(plan, host_points, n, s);
+        resIdx = plan->fOut;
+        resCnt = plan->stCnt + 4;
+    } else {
+        e = cudaMemcpyAsync(plan->stIn, host_points, sizeof(float) * 2 * (size_t)n, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_status(e);
-        plan->stCap = cap;
+        st = qh_hull2d_p(plan, plan->stIn, n, plan->stOut, plan->stCnt, stream);
     }
-    cudaError_t e = cudaMemcpyAsync(plan->stIn, host_points, sizeof(float) * 2 * (size_t)n, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    qh_status st = qh_hull2d_p(plan, plan->stIn, n, plan->stOut, plan->stCnt, stream);
     if (st != QH_OK) return st;
     // The count and the first indices come back together (one synchronisation for
     // every hull of up to EAGER vertices); a larger hull reads the rest after.
     constexpr long long EAGER = 65536;
     const long long first = n < EAGER ? n : EAGER;
-    e = cudaMemcpyAsync(host_out_count, plan->stCnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(host_out_count, resCnt, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && first > 0)
-        e = cudaMemcpyAsync(host_out_idx, plan->stOut, sizeof(int) * (size_t)first, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(host_out_idx, resIdx, sizeof(int) * (size_t)first, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     const int h = *host_out_count;
     if (h > first) {
-        e = cudaMemcpyAsync(host_out_idx + first, plan->stOut + first, sizeof(int) * (size_t)(h - first),
+        e = cudaMemcpyAsync(host_out_idx + first, resIdx + first, sizeof(int) * (size_t)(h - first),
                             cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_status(e);

@@ -249,6 +249,38 @@ def test_host_buffers(qh):
     plan.close()
 
 
+def test_host_buffers_overlapped(qh):
+    """The host-buffer entry point on sets of at least 2^22 points, where the copy of the
+    second half overlaps the hull of the first, and the first half's vertices are hulled
+    together with the second half: a disk of odd size, coordinate duplicates across the
+    halves (the first half's indices must win), equal points, a circle, and a non-finite
+    coordinate in the second half and in the first."""
+    plan = qh.Plan(5_000_000, 1)
+    disk = synth.disk(4_194_305, seed=12)
+    assert np.array_equal(qh.hull2d_host(disk, plan), oracle.hull2d(disk))
+    q = synth.disk(2_200_000, seed=13)
+    twice = np.concatenate([q, q])
+    got = qh.hull2d_host(twice, plan)
+    assert np.array_equal(got, oracle.hull2d(twice)) and got.max() < len(q)
+    same = np.full((4_300_000, 2), 0.75, dtype=np.float32)
+    assert qh.hull2d_host(same, plan).tolist() == [0]
+    ring = synth.circle(4_500_000, seed=14)
+    assert np.array_equal(qh.hull2d_host(ring, plan), oracle.hull2d(ring))
+    bad = synth.disk(4_500_000, seed=15)
+    bad[4_000_000, 1] = np.nan
+    with pytest.raises(qh.QhError) as e:
+        qh.hull2d_host(bad, plan)
+    assert e.value.status == 2
+    bad[4_000_000, 1] = 0.0
+    bad[10, 0] = np.inf
+    with pytest.raises(qh.QhError) as e:
+        qh.hull2d_host(bad, plan)
+    assert e.value.status == 2
+    small = synth.disk(100_000, seed=16)  # the direct path on the same plan afterwards
+    assert np.array_equal(qh.hull2d_host(small, plan), oracle.hull2d(small))
+    plan.close()
+
+
 def test_batched_degenerate_sets(qh):
     """One batched call over sets of every kind the front end classifies: empty, a
     single point, equal points (small and tiled), a tiled collinear line, a circle,
