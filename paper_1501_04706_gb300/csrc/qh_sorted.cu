@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(SNT) sx_radix_move(const unsigned *__restrict_
     }
 }
 
-// Sorted items -> polygon arrays of round 1, head positions, and the copy of A at T.
+// Sorted items -> polygon arrays of the first round, head positions, and the copy of A at T.
 __global__ void __launch_bounds__(SNT) sx_gather(const float2 *__restrict__ pts, int n, const unsigned *__restrict__ val,
                                                  SxBufs b, SxState *st, const Ctl *ctl) {
     const int K = st->K;
