@@ -220,7 +220,7 @@ qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t
  * the stream before returning.  Entries of host_out_idx past the count are
  * unspecified (the first min(n, 65536) entries are read back together with the
  * count).  Pinned host memory gives the fastest copies.
- * Sets of at least 2^22 points overlap the copy with the computation: the
+ * Sets of at least 11,000,000 points overlap the copy with the computation: the
  * second half is copied on a side stream of the plan while the first half is
  * hulled, then the first half's hull vertices are hulled together with the
  * second half (the same output).  The plan's statistics then describe that

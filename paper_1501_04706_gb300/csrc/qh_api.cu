@@ -637,8 +637,15 @@ qh_status qh_hull2d_sorted(qh_plan plan, const float *points, int64_t n, int32_t
 
 namespace {
 // Sets of at least this many points take the overlapped host path: the copy of
-// the second half runs on a side stream while the first half is hulled.
-constexpr long long HOST_SPLIT_MIN = 1ll << 22;
+// the second half runs on a side stream while the first half is hulled.  The
+// path pays a second hull call (~0.15 ms of fixed cost) to hide half of the
+// copy (~0.038 ms per million points at the host link's ~210 GB/s); on a GB300
+// it is slower below ~11M points (4.2M: 0.544 vs 0.469 ms, 10M: 0.832 vs 0.775
+// ms) and faster above (12M: 0.85 vs 0.88 ms, 20M: 1.17 vs 1.37 ms).
+#ifndef QH_HOST_SPLIT_MIN
+#define QH_HOST_SPLIT_MIN 11000000ll
+#endif
+constexpr long long HOST_SPLIT_MIN = QH_HOST_SPLIT_MIN;
 
 qh_status host_staging(qh_plan plan, long long n, bool split, cudaStream_t s) {
     if (plan->stCap >= n && plan->stIn && (!split || plan->mPts)) return QH_OK;

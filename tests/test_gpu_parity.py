@@ -250,28 +250,28 @@ def test_host_buffers(qh):
 
 
 def test_host_buffers_overlapped(qh):
-    """The host-buffer entry point on sets of at least 2^22 points, where the copy of the
+    """The host-buffer entry point on sets of at least 11M points, where the copy of the
     second half overlaps the hull of the first, and the first half's vertices are hulled
     together with the second half: a disk of odd size, coordinate duplicates across the
     halves (the first half's indices must win), equal points, a circle, and a non-finite
     coordinate in the second half and in the first."""
-    plan = qh.Plan(5_000_000, 1)
-    disk = synth.disk(4_194_305, seed=12)
+    plan = qh.Plan(11_600_000, 1)
+    disk = synth.disk(11_000_001, seed=12)
     assert np.array_equal(qh.hull2d_host(disk, plan), oracle.hull2d(disk))
-    q = synth.disk(2_200_000, seed=13)
+    q = synth.disk(5_600_000, seed=13)
     twice = np.concatenate([q, q])
     got = qh.hull2d_host(twice, plan)
     assert np.array_equal(got, oracle.hull2d(twice)) and got.max() < len(q)
-    same = np.full((4_300_000, 2), 0.75, dtype=np.float32)
+    same = np.full((11_100_000, 2), 0.75, dtype=np.float32)
     assert qh.hull2d_host(same, plan).tolist() == [0]
-    ring = synth.circle(4_500_000, seed=14)
+    ring = synth.circle(11_500_000, seed=14)
     assert np.array_equal(qh.hull2d_host(ring, plan), oracle.hull2d(ring))
-    bad = synth.disk(4_500_000, seed=15)
-    bad[4_000_000, 1] = np.nan
+    bad = synth.disk(11_500_000, seed=15)
+    bad[11_000_000, 1] = np.nan
     with pytest.raises(qh.QhError) as e:
         qh.hull2d_host(bad, plan)
     assert e.value.status == 2
-    bad[4_000_000, 1] = 0.0
+    bad[11_000_000, 1] = 0.0
     bad[10, 0] = np.inf
     with pytest.raises(qh.QhError) as e:
         qh.hull2d_host(bad, plan)
