@@ -34,6 +34,23 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_null_plan_rejected_without_a_device(lib):
+    """Every plan entry point checks its arguments before any CUDA call, so a null plan (or
+    negative size) is refused with QH_ERR_INVALID_ARG on a machine without a GPU too."""
+    import ctypes
+
+    x = (ctypes.c_float * 8)()
+    out = (ctypes.c_int32 * 4)()
+    cnt = ctypes.c_int32(0)
+    p, o, c = ctypes.addressof(x), ctypes.addressof(out), ctypes.byref(cnt)
+    assert lib.qh_hull2d_p(None, p, 4, o, c, None) == 1
+    assert lib.qh_hull2d_sorted(None, p, 4, o, c, None) == 1
+    assert lib.qh_hull2d_host(None, p, 4, o, c, None) == 1
+    assert lib.qh_hull2d_batched(None, p, None, 1, o, c, None) == 1
+    assert lib.qh_plan_destroy(None) == 0
+    assert lib.qh_check_orient_host(p, -1, 0, o, o) == 1
+
+
 def test_status_strings(lib):
     assert lib.qh_status_string(0) == b"ok"
     assert lib.qh_status_string(2) == b"non-finite input coordinate"
